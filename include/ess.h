@@ -1,0 +1,232 @@
+/*
+ * ess.h -- C ABI of libess: empty-space-skipping volume rendering on one
+ * NVIDIA GB300 (CUDA, sm_103a).
+ *
+ * The calls follow the problem statement of Zellmann, "Comparing Hierarchical
+ * Data Structures for Sparse Volume Rendering with Empty Space Skipping"
+ * (arXiv 1912.09596): a user edits the colour/alpha transfer function (TF),
+ * which changes which parts of the volume are empty, so a skipping index is
+ * rebuilt and the volume is ray-marched through it again (Sec. 1; Sec. 2
+ * contrasts this rebuild-per-change approach with updating an index).  Three index kinds are built (Sec. 3): a uniform macrocell grid
+ * (the baseline of Sec. 1 and 2), an LBVH over non-empty bricks (Sec. 3.1) and
+ * a k-d tree (Sec. 3.2).  Rendering is absorption plus emission with
+ * post-classification TF lookups (Sec. 4.1).
+ *
+ * Conventions
+ *  - Every call returns an ess_status; no C++ exception crosses the ABI.  On
+ *    failure ess_last_error() describes the cause.
+ *  - Inputs are copied: the caller keeps ownership of every input buffer and
+ *    may free or reuse it as soon as the call returns.
+ *  - Output images are caller-owned float32 RGBA buffers, W*H*4 floats, row
+ *    major, row 0 at the top.  `out_on_device` says whether `out` is device
+ *    memory (written asynchronously on the context stream) or host memory
+ *    (the call copies the image back and returns when it is there).
+ *  - Device memory that the library allocates belongs to the context and is
+ *    returned by ess_release() / ess_destroy().
+ *  - Work is issued asynchronously on the context's CUDA stream, in call
+ *    order.  ess_sync() waits for it and reports device-side errors.
+ *  - A context is used by one host thread at a time.
+ *  - World units are voxels: the volume box is [0,nx] x [0,ny] x [0,nz] and
+ *    voxel (i,j,k) has its centre at (i+0.5, j+0.5, k+0.5).
+ */
+#ifndef ESS_H
+#define ESS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ess_ctx ess_ctx;  /* opaque */
+typedef uint64_t ess_handle;     /* volume, TF or structure; 0 is invalid */
+
+typedef enum {
+    ESS_OK = 0,
+    ESS_ERR_ARG = -1,      /* invalid argument (message says which) */
+    ESS_ERR_OOM = -2,      /* device allocation failed */
+    ESS_ERR_CUDA = -3,     /* CUDA runtime error */
+    ESS_ERR_HANDLE = -4,   /* unknown, released or wrong-type handle */
+    ESS_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    ESS_ERR_BUSY = -6,     /* admission refused (memory budget) */
+    ESS_ERR_STALE = -7     /* structure built for an older TF: rebuild it */
+} ess_status;
+
+typedef enum { ESS_U8 = 0, ESS_U16 = 1, ESS_F32 = 2 } ess_dtype;
+
+typedef enum {
+    ESS_GRID = 0,  /* uniform macrocell grid = the brick mask (Sec. 1, 2) */
+    ESS_LBVH = 1,  /* LBVH over non-empty bricks (Sec. 3.1) */
+    ESS_KD = 2,    /* k-d tree with tight boxes (Sec. 3.2) */
+    ESS_NONE = 3   /* no skipping: naive ray marching (Table 2, "Naive") */
+} ess_kind;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`.  `cuda_stream` is the
+ * cudaStream_t to issue all work on (e.g. PyTorch's current stream); NULL
+ * means the CUDA default stream.  The caller keeps ownership of the stream. */
+ess_status ess_create(int device, void *cuda_stream, ess_ctx **out);
+
+/* Waits for outstanding work and frees everything the context owns. */
+ess_status ess_destroy(ess_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until
+ * the next call on the context. */
+const char *ess_last_error(const ess_ctx *ctx);
+
+/* Waits for all work issued on the context; returns a device-side error
+ * recorded since the last ess_sync (e.g. ESS_ERR_TIMEOUT), else ESS_OK. */
+ess_status ess_sync(ess_ctx *ctx);
+
+/* Releases a volume, TF or structure handle and its device memory.  A volume
+ * or TF still used by a live structure is kept until that structure goes. */
+ess_status ess_release(ess_ctx *ctx, ess_handle h);
+
+/* ----------------------------------------------------------------- inputs */
+
+/* Uploads a structured scalar volume (Sec. 4.2: uniform grids, in-core),
+ * `data` = nz*ny*nx voxels of `dtype`, x fastest.  `data_on_device` says
+ * whether `data` is device or host memory.  [value_lo, value_hi] is the value
+ * range mapped onto the TF (TF coordinate x = (v - value_lo) * (NT-1) /
+ * (value_hi - value_lo), clamped).  The call copies the data, so the caller
+ * keeps ownership.  Errors: ESS_ERR_ARG for a non-positive size, more than
+ * 8192 voxels on an axis, value_hi <= value_lo, or (f32) a NaN or infinite
+ * voxel; ESS_ERR_OOM if the copy does not fit. */
+ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
+                             ess_dtype dtype, int nx, int ny, int nz,
+                             float value_lo, float value_hi, ess_handle *vol);
+
+/* Sets an RGBA transfer function of `nt` entries (Sec. 1: the colour and
+ * alpha TF that maps scalar values to colour and opacity), `rgba` = nt*4
+ * floats, entry-major.  Alpha must lie in [0, 1] and every value must be
+ * finite.  2 <= nt <= 65536.  Copies the table. */
+ess_status ess_tf_set(ess_ctx *ctx, const float *rgba, int on_device, int nt,
+                      ess_handle *tf);
+
+/* Replaces the table of an existing TF in place (a TF edit, Sec. 1).  `nt`
+ * must equal the TF's size.  Structures built with the previous table become
+ * stale: ess_render on them returns ESS_ERR_STALE until ess_rebuild. */
+ess_status ess_tf_update(ess_ctx *ctx, ess_handle tf, const float *rgba, int on_device,
+                         int nt);
+
+/* -------------------------------------------------------------- structures */
+
+typedef struct {
+    int brick;   /* brick / macrocell edge B in voxels, 2..64 (Sec. 3.1: 8^3
+                    leaves; Sec. 3.2.2: 8^3 macro cells) */
+    int nbins;   /* k-d candidate planes per axis: 0 = every brick boundary
+                    (exhaustive, the CPU builder), else nbins - 1 binned
+                    planes (Sec. 3.2.2; 4 in Sec. 4.3) */
+    int halting; /* k-d halting (Sec. 4.3): 0 = shallow (split while the node
+                    volume is above 10 % of the root volume), 1 = deep (split
+                    while above 8^3 voxels) */
+    int mls;     /* k-d maximum leaf size (Sec. 4.3) as an edge in voxels
+                    (32 or 128 in the paper), 0 = none */
+    int empty_test; /* 0 = brick min/max range test (Sec. 2, min-max range
+                    queries), 1 = per-cell vote (Sec. 3.1 classifies per voxel) */
+} ess_build_params;
+
+/* Builds a skipping structure of `kind` for volume `vol` under TF `tf`
+ * (Sec. 3).  For ESS_NONE no index is built; the handle just binds the
+ * volume and the TF for naive rendering.  The structure keeps references to
+ * `vol` and `tf`.  Asynchronous except for the k-d build, which reads back
+ * one node count per tree level.  Errors: ESS_ERR_ARG for bad parameters,
+ * ESS_ERR_HANDLE for bad handles, ESS_ERR_OOM. */
+ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
+                     const ess_build_params *params, ess_handle *structure);
+
+/* Rebuilds `structure` for the current table of its TF (after ess_tf_update)
+ * reusing its device memory: the per-edit hot path of Sec. 1. */
+ess_status ess_rebuild(ess_ctx *ctx, ess_handle structure);
+
+typedef struct {
+    int kind, brick;
+    int gx, gy, gz;          /* brick grid = ceil(n / brick) per axis */
+    int64_t n_bricks;        /* gx*gy*gz */
+    int64_t n_nonempty;      /* non-empty bricks after the empty test */
+    int64_t n_nodes;         /* LBVH: 2n-1 (0 if n = 0); k-d: node count */
+    int height;              /* tree levels including root and leaves */
+    size_t device_bytes;     /* device memory held by the structure */
+} ess_structure_info;
+
+/* Fills `info` (waits for the structure's build to finish). */
+ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure,
+                                  ess_structure_info *info);
+
+typedef enum {
+    ESS_ARR_MINMAX = 0,      /* float32 [n_bricks][2]: apron min, max */
+    ESS_ARR_MASK = 1,        /* uint8  [n_bricks]: 1 = non-empty */
+    ESS_ARR_IDS = 2,         /* uint32 [n_nonempty]: non-empty brick ids, ascending */
+    ESS_ARR_KEYS = 3,        /* uint32 [n_nonempty]: Morton code of IDS[i] */
+    ESS_ARR_SORTED_KEYS = 4, /* uint32 [n_nonempty]: keys after the radix sort */
+    ESS_ARR_SORTED_IDS = 5,  /* uint32 [n_nonempty]: ids in sorted-key order */
+    ESS_ARR_LBVH_LEFT = 6,   /* int32 [n_nonempty-1]: left child (>= 0 inner,
+                                -1-j leaf j of the sorted order) */
+    ESS_ARR_LBVH_RIGHT = 7,  /* int32 [n_nonempty-1]: right child, same coding */
+    ESS_ARR_LBVH_BOXES = 8,  /* int32 [n_nonempty-1][6]: inner box lo xyz, hi xyz
+                                in brick coordinates, hi exclusive */
+    ESS_ARR_KD_NODES = 9     /* int32 [n_nodes][9]: lo xyz, hi xyz (bricks, hi
+                                exclusive), axis (-1 leaf), plane, first child
+                                (-1 leaf); breadth-first, left child first */
+} ess_array;
+
+/* Copies one array of a built structure to host memory `dst` of
+ * `capacity` bytes; `*written` receives the byte count.  Synchronous.
+ * ESS_ERR_ARG if the array does not exist for the structure's kind or does
+ * not fit. */
+ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array which,
+                              void *dst, size_t capacity, size_t *written);
+
+/* ------------------------------------------------------------------ render */
+
+typedef struct {
+    float eye[3];  /* perspective: ray origin; orthographic: view centre */
+    float u[3];    /* right, scaled: perspective tan(fov/2)*aspect, ortho half width */
+    float v[3];    /* up, scaled: perspective tan(fov/2), ortho half height */
+    float w[3];    /* forward (normalised before use) */
+    int ortho;     /* 1 = orthographic (Sec. 4.1), 0 = perspective */
+} ess_camera;
+
+typedef struct {
+    float dt;     /* step between samples in voxels, 1e-3 <= dt <= 1e4 */
+    float ert;    /* early ray termination: stop once opacity >= ert; a value
+                     above 1 disables it (the paper's benchmarks, Sec. 4.1) */
+    float bg[4];  /* background RGBA composited behind the volume */
+} ess_render_params;
+
+/* Ray-marches `structure` (Sec. 4.1: absorption plus emission,
+ * post-classification) into a W x H RGBA image.  Pixel (x, y) shoots the ray
+ * through sx = (2x+1)/W - 1, sy = 1 - (2y+1)/H; samples sit at
+ * t_k = t_near + k*dt on every path; skipping drops only samples of zero
+ * opacity, so the image equals naive marching.  ESS_ERR_STALE if the TF was
+ * updated after the build. */
+ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *camera,
+                      const ess_render_params *params, int W, int H, float *out,
+                      int out_on_device);
+
+/* -------------------------------------------------------------- profiling */
+
+/* Number of ray samples evaluated (classified and composited) by all renders
+ * on the context since it was created or last reset; waits for the work. */
+ess_status ess_sample_count(ess_ctx *ctx, uint64_t *samples, int reset);
+
+/* Kernel launch counter: number of CUDA kernels this context has launched. */
+uint64_t ess_launch_count(const ess_ctx *ctx);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default).
+ * While enabled, every launch is bracketed by events; ess_profile_read
+ * syncs, accumulates and returns, for each kernel name seen, its launch count
+ * and total milliseconds.  `names` receives up to `max` pointers to static
+ * strings. */
+ess_status ess_profile_enable(ess_ctx *ctx, int enable);
+ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names,
+                            uint64_t *launches, double *total_ms, int *count);
+ess_status ess_profile_reset(ess_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESS_H */

@@ -242,6 +242,32 @@ int64_t ora_render_naive(const ora_volume *V, const ora_tf *T, const ora_camera 
     return nsamp;
 }
 
+/* Naive marching of a list of pixels (x, y pairs): the same definition as
+ * ora_render_naive, for spot checks of large images.  out: 4 floats per pixel. */
+int64_t ora_render_pixels(const ora_volume *V, const ora_tf *T, const ora_camera *C,
+                          const ora_render_params *P, int W, int H, const int32_t *xy, int n,
+                          float *out)
+{
+    float s = ora_tf_scale(V, T->nt);
+    int64_t nsamp = 0;
+    for (int i = 0; i < n; ++i) {
+        float o[3], d[3], tn, tf;
+        ora_acc acc = {{0.0f, 0.0f, 0.0f}, 0.0f};
+        ora_ray(C, xy[2 * i], xy[2 * i + 1], W, H, o, d);
+        volume_interval(V, o, d, &tn, &tf);
+        if (tn < tf) {
+            for (int k = 0;; ++k) {
+                float t = fmaf((float)k, P->dt, tn);
+                if (!(t < tf)) break;
+                ++nsamp;
+                if (composite_sample(V, T, s, o, d, t, P->ert, &acc)) break;
+            }
+        }
+        finish_pixel(&acc, P->bg, out + 4 * (size_t)i);
+    }
+    return nsamp;
+}
+
 /* Rendering with skipping, by brute force (rule S).  `boxes` holds nbox
  * closed boxes [lo, hi] in voxel units (6 floats each) that together cover
  * every region whose samples may be non-zero (non-empty bricks or tree

@@ -76,6 +76,9 @@ def lib():
             L.ora_render_naive.argtypes = [P(Volume), P(TF), P(Camera), P(RenderParams),
                                            i, i, vp, i, i]
             L.ora_render_naive.restype = C.c_int64
+            L.ora_render_pixels.argtypes = [P(Volume), P(TF), P(Camera), P(RenderParams),
+                                            i, i, vp, i, vp]
+            L.ora_render_pixels.restype = C.c_int64
             L.ora_render_boxes.argtypes = [P(Volume), P(TF), P(Camera), P(RenderParams),
                                            i, i, vp, i, vp, i, i]
             L.ora_render_boxes.restype = C.c_int64
@@ -206,6 +209,29 @@ def render_naive(vol: OVolume, tf: OTF, cam, W, H, dt=0.5, ert=2.0,
             t.start()
         for t in ts:
             t.join()
+    return out, int(sum(counts))
+
+
+def render_pixels(vol: OVolume, tf: OTF, cam, W, H, xy, dt=0.5, ert=2.0,
+                  bg=(0.0, 0.0, 0.0, 0.0), threads=1):
+    """Naive marching of the pixels `xy` ((n, 2) int: x, y).  Returns (n, 4)."""
+    xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
+    out = np.zeros((xy.shape[0], 4), dtype=np.float32)
+    cs, ps = camera_struct(cam), params_struct(dt, ert, bg)
+    L = lib()
+    counts = []
+
+    def work(a, b):
+        counts.append(L.ora_render_pixels(C.byref(vol.c), C.byref(tf.c), C.byref(cs),
+                                          C.byref(ps), W, H, _p(xy[a:b]), b - a,
+                                          _p(out[a:b])))
+
+    bands = _row_split(xy.shape[0], threads)
+    ts = [threading.Thread(target=work, args=b) for b in bands]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
     return out, int(sum(counts))
 
 

@@ -1,0 +1,382 @@
+// classify.cu -- the empty test: per-brick apron min/max (once per volume and
+// brick size), TF prefix counts, the min/max range test that yields the brick
+// mask, the per-cell vote variant, and stream compaction of the non-empty
+// bricks (Sec. 3.1 compacts the brick list to the non-empty bricks before
+// assigning Morton codes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ess_internal.h"
+
+namespace ess {
+
+// ------------------------------------------------------------------ helpers
+template <typename T> __device__ __forceinline__ float to_f(T v) { return (float)v; }
+
+__device__ __forceinline__ float tf_coord(float v, float value_lo, float s, float xmax)
+{
+    float x = (v - value_lo) * s;
+    x = x < 0.0f ? 0.0f : x;
+    x = x > xmax ? xmax : x;
+    return x;
+}
+
+// ------------------------------------------------------------ finite check
+__global__ void k_check_finite(const float *__restrict__ v, size_t n, uint32_t *status)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) bad |= !isfinite(v[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, DEV_ERR_NONFINITE);
+}
+
+void launch_check_finite(Ctx &c, const float *v, size_t n)
+{
+    Launch L(c, "check_finite");
+    k_check_finite<<<152 * 8, 256, 0, c.stream>>>(v, n, c.dev_status);
+}
+
+// ------------------------------------------------------------ K1 min/max
+// Brick b covers voxels [bB, (b+1)B) and its samples read the apron range
+// [bB-1, (b+1)B] (clamped to the volume), so min/max run over that range.
+// One warp per (by, bz) and run of 32 bricks along x: lane l owns brick
+// bx = 32*seg + l and walks its (B+2)^2 apron rows; the 32 lanes of a warp
+// read one contiguous stretch of each row, so the loads coalesce and the
+// apron overlap between neighbours is served by L1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_brick_minmax(const T *__restrict__ vol, int nx,
+                                                      int ny, int nz, int B, int gx, int gy,
+                                                      int gz, float2 *__restrict__ out)
+{
+    int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    int nseg = (gx + 31) >> 5;
+    int total = nseg * gy * gz;
+    if (warp >= total) return;
+    int seg = warp % nseg;
+    int rest = warp / nseg;
+    int by = rest % gy, bz = rest / gy;
+    int bx = seg * 32 + lane;
+    if (bx >= gx) return;
+    int x0 = max(bx * B - 1, 0), x1 = min((bx + 1) * B, nx - 1);
+    int y0 = max(by * B - 1, 0), y1 = min((by + 1) * B, ny - 1);
+    int z0 = max(bz * B - 1, 0), z1 = min((bz + 1) * B, nz - 1);
+    float mn = INFINITY, mx = -INFINITY;
+    for (int z = z0; z <= z1; ++z) {
+        for (int y = y0; y <= y1; ++y) {
+            const T *row = vol + ((size_t)z * ny + y) * (size_t)nx;
+            for (int x = x0; x <= x1; ++x) {
+                float v = to_f(__ldg(row + x));
+                mn = v < mn ? v : mn;
+                mx = v > mx ? v : mx;
+            }
+        }
+    }
+    out[((size_t)bz * gy + by) * gx + bx] = make_float2(mn, mx);
+}
+
+void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out)
+{
+    int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
+    size_t warps = (size_t)((gx + 31) / 32) * gy * gz;
+    unsigned blocks = (unsigned)((warps + 7) / 8);
+    Launch L(c, "brick_minmax");
+    switch (v.dtype) {
+    case ESS_U8:
+        k_brick_minmax<uint8_t><<<blocks, 256, 0, c.stream>>>((const uint8_t *)v.data, v.nx, v.ny,
+                                                              v.nz, B, gx, gy, gz, out);
+        break;
+    case ESS_U16:
+        k_brick_minmax<uint16_t><<<blocks, 256, 0, c.stream>>>((const uint16_t *)v.data, v.nx,
+                                                               v.ny, v.nz, B, gx, gy, gz, out);
+        break;
+    default:
+        k_brick_minmax<float><<<blocks, 256, 0, c.stream>>>((const float *)v.data, v.nx, v.ny,
+                                                            v.nz, B, gx, gy, gz, out);
+    }
+}
+
+// --------------------------------------------------------- K2 TF prefix
+// prefix[i] = #{j < i : alpha_j > 0}, i = 0..nt (one block).
+__global__ void __launch_bounds__(1024) k_tf_prefix(const float4 *__restrict__ table, int nt,
+                                                    int *__restrict__ prefix)
+{
+    __shared__ int warp_tot[32];
+    int t = threadIdx.x;
+    int per = (nt + 1023) / 1024;
+    int b0 = t * per, b1 = min(nt, b0 + per);
+    int cnt = 0;
+    for (int i = b0; i < b1; ++i) cnt += table[i].w > 0.0f ? 1 : 0;
+    // block-wide exclusive scan of cnt
+    int lane = t & 31, w = t >> 5;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int s = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_tot[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    int base = (w > 0 ? warp_tot[w - 1] : 0) + incl - cnt;
+    for (int i = b0; i < b1; ++i) {
+        prefix[i] = base;
+        base += table[i].w > 0.0f ? 1 : 0;
+    }
+    if (t == 1023) prefix[nt] = warp_tot[31];
+}
+
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix)
+{
+    Launch L(c, "tf_prefix");
+    k_tf_prefix<<<1, 1024, 0, c.stream>>>(table, nt, prefix);
+}
+
+// ---------------------------------------------------- K2 range test (mask)
+// Every sample of a brick has a value in [min, max] of its apron (a lerp
+// fmaf(f, b - a, a) with f in [0, 1) never leaves [a, b]); with x() monotone
+// it reads TF entries floor(x(min)) .. floor(x(max)) + 1 only, so the brick is
+// non-empty iff one of those entries has alpha > 0 (prefix-count difference).
+__global__ void k_brick_mask(const float2 *__restrict__ minmax, int64_t nb,
+                             const int *__restrict__ prefix, int nt, float value_lo, float s,
+                             uint8_t *__restrict__ mask)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    float2 m = minmax[b];
+    float xmax = (float)(nt - 1);
+    int lo = (int)tf_coord(m.x, value_lo, s, xmax);
+    int hi = (int)tf_coord(m.y, value_lo, s, xmax) + 1;
+    hi = hi > nt - 1 ? nt - 1 : hi;
+    mask[b] = (__ldg(prefix + hi + 1) - __ldg(prefix + lo)) > 0 ? 1 : 0;
+}
+
+void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf, float value_lo,
+                       float s, uint8_t *mask)
+{
+    Launch L(c, "brick_mask");
+    unsigned blocks = (unsigned)((nb + 255) / 256);
+    k_brick_mask<<<blocks, 256, 0, c.stream>>>(minmax, nb, tf.prefix, tf.nt, value_lo, s, mask);
+}
+
+// ------------------------------------------------ per-cell vote variant
+// The paper's LBVH classifier decides visibility per voxel and lets the
+// threads of a brick vote through a shared-memory flag (Sec. 3.1).  The
+// conservative form of that vote for interpolated samples: one thread per
+// trilinear cell c (corner voxels c..c+1, clamped; c in [-1, n-1]) tests the
+// range of its 8 corner values; a positive cell marks every brick whose closed
+// region its sample region [c+0.5, c+1.5) touches, with an idempotent store
+// of 1.  A block covers an 8x8x4 tile of cells and leaves early when none of
+// its cells is positive.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mask_cells(const T *__restrict__ vol, int nx, int ny,
+                                                    int nz, int B, int gx, int gy, int gz,
+                                                    const int *__restrict__ prefix, int nt,
+                                                    float value_lo, float s,
+                                                    uint8_t *__restrict__ mask)
+{
+    // tile origin in cell coordinates (cells start at -1)
+    int cx = blockIdx.x * 8 + (threadIdx.x & 7) - 1;
+    int cy = blockIdx.y * 8 + ((threadIdx.x >> 3) & 7) - 1;
+    int cz = blockIdx.z * 4 + (threadIdx.x >> 6) - 1;
+    bool pos = false;
+    if (cx < nx && cy < ny && cz < nz) {
+        int x0 = max(cx, 0), x1 = min(cx + 1, nx - 1);
+        int y0 = max(cy, 0), y1 = min(cy + 1, ny - 1);
+        int z0 = max(cz, 0), z1 = min(cz + 1, nz - 1);
+        float mn = INFINITY, mx = -INFINITY;
+#pragma unroll
+        for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 2; ++dx) {
+                    size_t idx = ((size_t)(dz ? z1 : z0) * ny + (dy ? y1 : y0)) * (size_t)nx +
+                                 (dx ? x1 : x0);
+                    float v = to_f(__ldg(vol + idx));
+                    mn = v < mn ? v : mn;
+                    mx = v > mx ? v : mx;
+                }
+        float xmax = (float)(nt - 1);
+        int lo = (int)tf_coord(mn, value_lo, s, xmax);
+        int hi = (int)tf_coord(mx, value_lo, s, xmax) + 1;
+        hi = hi > nt - 1 ? nt - 1 : hi;
+        pos = (__ldg(prefix + hi + 1) - __ldg(prefix + lo)) > 0;
+    }
+    if (!__syncthreads_or(pos)) return;
+    if (!pos) return;
+    // bricks b with 2c+1 <= 2*min((b+1)B, n) and 2c+3 >= 2bB, per axis; as
+    // c <= n-1 the clamp at n never decides the first condition
+    int c[3] = {cx, cy, cz}, g[3] = {gx, gy, gz};
+    int blo[3], bhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // lowest b: need (b+1)B >= c + 0.5 (or the clamp at n): b >= ceil((c+0.5)/B) - 1
+        int lo = (2 * c[a] + 1 + 2 * B - 1) / (2 * B) - 1;
+        if (2 * c[a] + 1 < 0) lo = 0;
+        lo = max(lo, 0);
+        // highest b: need bB <= c + 1.5: b <= floor((2c+3)/(2B))
+        int hi = (2 * c[a] + 3) / (2 * B);
+        hi = min(hi, g[a] - 1);
+        blo[a] = lo;
+        bhi[a] = hi;
+    }
+    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
+        for (int by = blo[1]; by <= bhi[1]; ++by)
+            for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
+                uint8_t *f = mask + ((size_t)bz * gy + by) * gx + bx;
+                if (*(volatile uint8_t *)f == 0) *f = 1;
+            }
+}
+
+void launch_brick_mask_cells(Ctx &c, const Volume &v, int B, const TF &tf, float s, uint8_t *mask,
+                             int gx, int gy, int gz)
+{
+    ESS_CUDA(cudaMemsetAsync(mask, 0, (size_t)gx * gy * gz, c.stream));
+    dim3 grid((v.nx + 1 + 7) / 8, (v.ny + 1 + 7) / 8, (v.nz + 1 + 3) / 4);
+    Launch L(c, "mask_cells");
+    switch (v.dtype) {
+    case ESS_U8:
+        k_mask_cells<uint8_t><<<grid, 256, 0, c.stream>>>((const uint8_t *)v.data, v.nx, v.ny, v.nz,
+                                                          B, gx, gy, gz, tf.prefix, tf.nt,
+                                                          v.value_lo, s, mask);
+        break;
+    case ESS_U16:
+        k_mask_cells<uint16_t><<<grid, 256, 0, c.stream>>>((const uint16_t *)v.data, v.nx, v.ny,
+                                                           v.nz, B, gx, gy, gz, tf.prefix, tf.nt,
+                                                           v.value_lo, s, mask);
+        break;
+    default:
+        k_mask_cells<float><<<grid, 256, 0, c.stream>>>((const float *)v.data, v.nx, v.ny, v.nz, B,
+                                                        gx, gy, gz, tf.prefix, tf.nt, v.value_lo,
+                                                        s, mask);
+    }
+}
+
+// ------------------------------------------------------------ K3 compaction
+// Three passes over the byte mask: per-tile counts, one-block scan of the
+// tile counts (also the total), per-tile scatter with a block-local scan, so
+// the ids come out in ascending order.  A tile is 256 threads x 16 flags,
+// each thread reading its flags as one 16-byte vector (the mask buffer is
+// padded to whole tiles and zero-filled).
+constexpr int CT_THREADS = 256;
+constexpr int CT_ITEMS = 16;
+constexpr int CT_TILE = CT_THREADS * CT_ITEMS;
+
+size_t compact_block_count(int64_t nb) { return (size_t)((nb + CT_TILE - 1) / CT_TILE); }
+
+__device__ __forceinline__ int popc_bytes(uint4 v)
+{
+    // each byte is 0 or 1
+    uint32_t s = v.x + v.y + v.z + v.w;  // per-byte sums stay < 256
+    return (int)((s & 0xffu) + ((s >> 8) & 0xffu) + ((s >> 16) & 0xffu) + (s >> 24));
+}
+
+template <int NT>
+__device__ __forceinline__ int block_excl_scan(int v, int &total)
+{
+    __shared__ int wsum[NT / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    total = wsum[NT / 32 - 1];
+    int r = (w > 0 ? wsum[w - 1] : 0) + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(CT_THREADS) k_compact_count(const uint8_t *__restrict__ mask,
+                                                              uint32_t *__restrict__ block_sums)
+{
+    const uint4 *m = reinterpret_cast<const uint4 *>(mask) + (size_t)blockIdx.x * CT_THREADS;
+    int c = popc_bytes(m[threadIdx.x]);
+    int total;
+    block_excl_scan<CT_THREADS>(c, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = (uint32_t)total;
+}
+
+// exclusive scan of nblk tile counts in one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_compact_scan(uint32_t *__restrict__ block_sums,
+                                                       int nblk, int *__restrict__ count)
+{
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblk; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < nblk ? (int)block_sums[i] : 0;
+        int total;
+        int ex = block_excl_scan<1024>(v, total);
+        if (i < nblk) block_sums[i] = (uint32_t)(carry + ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void __launch_bounds__(CT_THREADS) k_compact_scatter(const uint8_t *__restrict__ mask,
+                                                                const uint32_t *__restrict__ block_sums,
+                                                                int64_t nb, uint32_t *__restrict__ ids)
+{
+    const uint4 *m = reinterpret_cast<const uint4 *>(mask) + (size_t)blockIdx.x * CT_THREADS;
+    uint4 v = m[threadIdx.x];
+    int c = popc_bytes(v);
+    int total;
+    int off = block_excl_scan<CT_THREADS>(c, total) + (int)block_sums[blockIdx.x];
+    if (c == 0) return;
+    int64_t first = (int64_t)blockIdx.x * CT_TILE + (int64_t)threadIdx.x * CT_ITEMS;
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < CT_ITEMS; ++j) {
+        if ((w[j >> 2] >> (8 * (j & 3))) & 0xffu) {
+            int64_t b = first + j;
+            if (b < nb) ids[off] = (uint32_t)b;
+            ++off;
+        }
+    }
+}
+
+void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int *count,
+                    uint32_t *block_sums)
+{
+    unsigned nblk = (unsigned)compact_block_count(nb);
+    {
+        Launch L(c, "compact_count");
+        k_compact_count<<<nblk, CT_THREADS, 0, c.stream>>>(mask, block_sums);
+    }
+    {
+        Launch L(c, "compact_scan");
+        k_compact_scan<<<1, 1024, 0, c.stream>>>(block_sums, (int)nblk, count);
+    }
+    {
+        Launch L(c, "compact_scatter");
+        k_compact_scatter<<<nblk, CT_THREADS, 0, c.stream>>>(mask, block_sums, nb, ids);
+    }
+}
+
+}  // namespace ess

@@ -1,0 +1,647 @@
+// ctx.cpp -- host orchestration behind the C ABI of include/ess.h: context,
+// handles, stream-ordered device memory, input validation, build dispatch,
+// render dispatch, read-back and profiling.  All device work goes to the
+// context stream; nothing here computes on the CPU what a kernel computes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ess_internal.h"
+
+struct ess_ctx {
+    ess::Ctx c;
+};
+
+namespace ess {
+
+// ------------------------------------------------------------ memory, events
+void *Ctx::alloc(size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{ESS_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    }
+    return p;
+}
+
+void Ctx::free(void *p)
+{
+    if (p) cudaFreeAsync(p, stream);
+}
+
+cudaEvent_t Ctx::event()
+{
+    if (!free_events.empty()) {
+        cudaEvent_t e = free_events.back();
+        free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    ESS_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Ctx::begin(const char *name)
+{
+    ++launches;
+    current = name;
+    if (profiling) {
+        cur_a = event();
+        cudaEventRecord(cur_a, stream);
+    }
+}
+
+void Ctx::end()
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        throw Error{ESS_ERR_CUDA, std::string("launch of ") + (current ? current : "?") + ": " +
+                                      cudaGetErrorString(e)};
+    if (profiling && current) {
+        cudaEvent_t b = event();
+        cudaEventRecord(b, stream);
+        pending.push_back({current, cur_a, b});
+    }
+    current = nullptr;
+}
+
+}  // namespace ess
+
+using namespace ess;
+
+namespace {
+
+enum : uint64_t { TAG_VOL = 1, TAG_TF = 2, TAG_ST = 3 };
+
+ess_handle new_handle(Ctx &c, uint64_t tag) { return (tag << 56) | (c.next_handle++); }
+
+template <typename F> ess_status guard(ess_ctx *ctx, F &&f)
+{
+    if (!ctx) return ESS_ERR_ARG;
+    Ctx &c = ctx->c;
+    c.last_error.clear();
+    try {
+        ESS_CUDA(cudaSetDevice(c.device));
+        f(c);
+        return ESS_OK;
+    } catch (const Error &e) {
+        c.last_error = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        c.last_error = "host allocation failed";
+        return ESS_ERR_OOM;
+    } catch (...) {
+        c.last_error = "unexpected internal error";
+        return ESS_ERR_CUDA;
+    }
+}
+
+Volume &get_vol(Ctx &c, ess_handle h)
+{
+    auto it = c.volumes.find(h);
+    if (it == c.volumes.end() || it->second->released)
+        throw Error{ESS_ERR_HANDLE, "unknown volume handle"};
+    return *it->second;
+}
+
+TF &get_tf(Ctx &c, ess_handle h)
+{
+    auto it = c.tfs.find(h);
+    if (it == c.tfs.end() || it->second->released) throw Error{ESS_ERR_HANDLE, "unknown TF handle"};
+    return *it->second;
+}
+
+Structure &get_st(Ctx &c, ess_handle h)
+{
+    auto it = c.structures.find(h);
+    if (it == c.structures.end() || it->second->released)
+        throw Error{ESS_ERR_HANDLE, "unknown structure handle"};
+    return *it->second;
+}
+
+size_t dtype_size(ess_dtype d) { return d == ESS_U8 ? 1 : (d == ESS_U16 ? 2 : 4); }
+
+// Reads and clears the device status word (synchronises the stream).
+ess_status take_status(Ctx &c, std::string &msg)
+{
+    ESS_CUDA(cudaMemcpyAsync(c.host_status, c.dev_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             c.stream));
+    ESS_CUDA(cudaStreamSynchronize(c.stream));
+    uint32_t s = *c.host_status;
+    if (!s) return ESS_OK;
+    ESS_CUDA(cudaMemsetAsync(c.dev_status, 0, sizeof(uint32_t), c.stream));
+    if (s & DEV_ERR_TIMEOUT) {
+        msg = "a bounded device-side wait gave up";
+        return ESS_ERR_TIMEOUT;
+    }
+    if (s & DEV_ERR_OVERFLOW) {
+        msg = "a device buffer reached its capacity";
+        return ESS_ERR_ARG;
+    }
+    msg = "volume holds a NaN or infinite value";
+    return ESS_ERR_ARG;
+}
+
+void check_tf_host(const float *rgba, int nt)
+{
+    for (int i = 0; i < 4 * nt; ++i) {
+        float v = rgba[i];
+        if (!std::isfinite(v)) throw Error{ESS_ERR_ARG, "TF holds a NaN or infinite value"};
+        if ((i & 3) == 3 && (v < 0.0f || v > 1.0f))
+            throw Error{ESS_ERR_ARG, "TF alpha outside [0, 1]"};
+    }
+}
+
+// Copies a TF table (host or device) into `t`, validating it on the host.
+void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
+{
+    std::vector<float> h((size_t)t.nt * 4);
+    if (on_device) {
+        ESS_CUDA(cudaMemcpyAsync(h.data(), rgba, h.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                 c.stream));
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+    } else {
+        std::memcpy(h.data(), rgba, h.size() * sizeof(float));
+    }
+    check_tf_host(h.data(), t.nt);
+    if (on_device) {
+        ESS_CUDA(cudaMemcpyAsync(t.table, rgba, h.size() * sizeof(float), cudaMemcpyDeviceToDevice,
+                                 c.stream));
+    } else {
+        // pinned staging so that the copy is truly asynchronous and the caller's
+        // buffer is free on return
+        if (!t.staging) ESS_CUDA(cudaMallocHost(&t.staging, h.size() * sizeof(float)));
+        if (t.staged) ESS_CUDA(cudaEventSynchronize(t.staged));
+        std::memcpy(t.staging, h.data(), h.size() * sizeof(float));
+        ESS_CUDA(cudaMemcpyAsync(t.table, t.staging, h.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, c.stream));
+        if (!t.staged) ESS_CUDA(cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
+        ESS_CUDA(cudaEventRecord(t.staged, c.stream));
+    }
+    launch_tf_prefix(c, t.table, t.nt, t.prefix);
+    ++t.version;
+}
+
+float2 *minmax_for(Ctx &c, Volume &v, int B)
+{
+    auto it = v.minmax.find(B);
+    if (it != v.minmax.end()) return it->second;
+    int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
+    float2 *mm = (float2 *)c.alloc(sizeof(float2) * (size_t)gx * gy * gz);
+    launch_brick_minmax(c, v, B, mm);
+    v.minmax[B] = mm;
+    return mm;
+}
+
+void free_structure(Ctx &c, Structure &s)
+{
+    void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_alt, s.ids_sorted,
+                    s.ids_alt, s.sort_scratch, s.left, s.right, s.parent, s.leaf_parent,
+                    s.inner_box, s.arrive, s.nodes, s.kd_nodes, s.kd_leaf_box, s.kd_aux,
+                    s.brick_node};
+    for (void *p : ptrs) c.free(p);
+}
+
+// The empty test and compaction (Sec. 3.1), then the kind-specific build.
+void run_build(Ctx &c, Structure &s)
+{
+    Volume &v = get_vol(c, s.vol);
+    TF &t = get_tf(c, s.tf);
+    int B = s.p.brick;
+    float sc = (float)(t.nt - 1) / (v.value_hi - v.value_lo);
+    if (s.p.empty_test == 1) {
+        launch_brick_mask_cells(c, v, B, t, sc, s.mask, s.gx, s.gy, s.gz);
+    } else {
+        float2 *mm = minmax_for(c, v, B);
+        launch_brick_mask(c, mm, s.nb, t, v.value_lo, sc, s.mask);
+    }
+    launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums);
+    s.n_host = -1;
+    s.tf_version = t.version;
+}
+
+int64_t nonempty_count(Ctx &c, Structure &s)
+{
+    if (s.n_host < 0) {
+        int n = 0;
+        ESS_CUDA(cudaMemcpyAsync(&n, s.count, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        s.n_host = n;
+    }
+    return s.n_host;
+}
+
+void copy_out(Ctx &c, void *dst, const void *src, size_t bytes, size_t cap, size_t *written)
+{
+    if (bytes > cap) throw Error{ESS_ERR_ARG, "destination buffer too small"};
+    if (bytes) ESS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c.stream));
+    ESS_CUDA(cudaStreamSynchronize(c.stream));
+    if (written) *written = bytes;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+ess_status ess_create(int device, void *cuda_stream, ess_ctx **out)
+{
+    if (!out) return ESS_ERR_ARG;
+    *out = nullptr;
+    ess_ctx *ctx = new (std::nothrow) ess_ctx();
+    if (!ctx) return ESS_ERR_OOM;
+    Ctx &c = ctx->c;
+    c.device = device;
+    ess_status st = guard(ctx, [&](Ctx &c) {
+        c.stream = (cudaStream_t)cuda_stream;  // NULL: the CUDA default stream
+        c.own_stream = false;
+        ESS_CUDA(cudaMalloc(&c.dev_status, sizeof(uint32_t)));
+        ESS_CUDA(cudaMemset(c.dev_status, 0, sizeof(uint32_t)));
+        ESS_CUDA(cudaMalloc(&c.samples, sizeof(unsigned long long)));
+        ESS_CUDA(cudaMemset(c.samples, 0, sizeof(unsigned long long)));
+        ESS_CUDA(cudaMallocHost(&c.host_status, sizeof(uint32_t)));
+    });
+    if (st != ESS_OK) {
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return ESS_OK;
+}
+
+ess_status ess_destroy(ess_ctx *ctx)
+{
+    if (!ctx) return ESS_ERR_ARG;
+    ess_status st = guard(ctx, [&](Ctx &c) {
+        for (auto &kv : c.structures) free_structure(c, *kv.second);
+        for (auto &kv : c.volumes) {
+            c.free(kv.second->data);
+            for (auto &m : kv.second->minmax) c.free(m.second);
+        }
+        for (auto &kv : c.tfs) {
+            c.free(kv.second->table);
+            c.free(kv.second->prefix);
+        }
+        c.free(c.stage);
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        for (auto &kv : c.tfs) {
+            if (kv.second->staging) cudaFreeHost(kv.second->staging);
+            if (kv.second->staged) cudaEventDestroy(kv.second->staged);
+        }
+        for (auto &p : c.pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : c.free_events) cudaEventDestroy(e);
+        cudaFree(c.dev_status);
+        cudaFree(c.samples);
+        cudaFreeHost(c.host_status);
+        if (c.own_stream) cudaStreamDestroy(c.stream);
+    });
+    delete ctx;
+    return st;
+}
+
+const char *ess_last_error(const ess_ctx *ctx)
+{
+    return ctx ? ctx->c.last_error.c_str() : "null context";
+}
+
+ess_status ess_sync(ess_ctx *ctx)
+{
+    ess_status dev = ESS_OK;
+    std::string msg;
+    ess_status st = guard(ctx, [&](Ctx &c) { dev = take_status(c, msg); });
+    if (st != ESS_OK) return st;
+    if (dev != ESS_OK) ctx->c.last_error = msg;
+    return dev;
+}
+
+ess_status ess_release(ess_ctx *ctx, ess_handle h)
+{
+    return guard(ctx, [&](Ctx &c) {
+        uint64_t tag = h >> 56;
+        if (tag == TAG_ST) {
+            Structure &s = get_st(c, h);
+            free_structure(c, s);
+            get_vol(c, s.vol).refs--;
+            get_tf(c, s.tf).refs--;
+            c.structures.erase(h);
+        } else if (tag == TAG_VOL) {
+            Volume &v = get_vol(c, h);
+            if (v.refs > 0) throw Error{ESS_ERR_ARG, "volume still used by a structure"};
+            c.free(v.data);
+            for (auto &m : v.minmax) c.free(m.second);
+            c.volumes.erase(h);
+        } else if (tag == TAG_TF) {
+            TF &t = get_tf(c, h);
+            if (t.refs > 0) throw Error{ESS_ERR_ARG, "TF still used by a structure"};
+            c.free(t.table);
+            c.free(t.prefix);
+            ESS_CUDA(cudaStreamSynchronize(c.stream));
+            if (t.staging) cudaFreeHost(t.staging);
+            if (t.staged) cudaEventDestroy(t.staged);
+            c.tfs.erase(h);
+        } else {
+            throw Error{ESS_ERR_HANDLE, "unknown handle"};
+        }
+    });
+}
+
+ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device, ess_dtype dtype,
+                             int nx, int ny, int nz, float value_lo, float value_hi,
+                             ess_handle *vol)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(data && vol, "null pointer");
+        ESS_REQUIRE(dtype == ESS_U8 || dtype == ESS_U16 || dtype == ESS_F32, "bad dtype");
+        ESS_REQUIRE(nx > 0 && ny > 0 && nz > 0 && nx <= 8192 && ny <= 8192 && nz <= 8192,
+                    "volume dimensions must be in 1..8192");
+        ESS_REQUIRE(std::isfinite(value_lo) && std::isfinite(value_hi) && value_hi > value_lo,
+                    "value range must be finite with value_hi > value_lo");
+        auto v = std::make_unique<Volume>();
+        v->nx = nx;
+        v->ny = ny;
+        v->nz = nz;
+        v->dtype = dtype;
+        v->value_lo = value_lo;
+        v->value_hi = value_hi;
+        v->bytes = (size_t)nx * ny * nz * dtype_size(dtype);
+        v->data = c.alloc(v->bytes);
+        cudaError_t e = cudaMemcpyAsync(v->data, data, v->bytes,
+                                        data_on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                                        c.stream);
+        if (e == cudaSuccess && !data_on_device) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) {
+            c.free(v->data);
+            throw Error{ESS_ERR_CUDA, std::string("volume copy: ") + cudaGetErrorString(e)};
+        }
+        if (dtype == ESS_F32) {
+            launch_check_finite(c, (const float *)v->data, (size_t)nx * ny * nz);
+            std::string msg;
+            if (take_status(c, msg) != ESS_OK) {
+                c.free(v->data);
+                throw Error{ESS_ERR_ARG, msg};
+            }
+        }
+        ess_handle h = new_handle(c, TAG_VOL);
+        c.volumes[h] = std::move(v);
+        *vol = h;
+    });
+}
+
+ess_status ess_tf_set(ess_ctx *ctx, const float *rgba, int on_device, int nt, ess_handle *tf)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(rgba && tf, "null pointer");
+        ESS_REQUIRE(nt >= 2 && nt <= 65536, "nt must be in 2..65536");
+        auto t = std::make_unique<TF>();
+        t->nt = nt;
+        t->table = (float4 *)c.alloc(sizeof(float4) * nt);
+        t->prefix = (int *)c.alloc(sizeof(int) * (nt + 1));
+        try {
+            load_tf(c, *t, rgba, on_device);
+        } catch (...) {
+            c.free(t->table);
+            c.free(t->prefix);
+            throw;
+        }
+        ess_handle h = new_handle(c, TAG_TF);
+        c.tfs[h] = std::move(t);
+        *tf = h;
+    });
+}
+
+ess_status ess_tf_update(ess_ctx *ctx, ess_handle tf, const float *rgba, int on_device, int nt)
+{
+    return guard(ctx, [&](Ctx &c) {
+        TF &t = get_tf(c, tf);
+        ESS_REQUIRE(rgba, "null pointer");
+        ESS_REQUIRE(nt == t.nt, "TF update must keep the table size");
+        load_tf(c, t, rgba, on_device);
+    });
+}
+
+ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
+                     const ess_build_params *params, ess_handle *structure)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(structure, "null pointer");
+        Volume &v = get_vol(c, vol);
+        TF &t = get_tf(c, tf);
+        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_NONE,
+                    "structure kind not available in this build");
+        ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0};
+        auto s = std::make_unique<Structure>();
+        s->kind = kind;
+        s->vol = vol;
+        s->tf = tf;
+        if (kind != ESS_NONE) {
+            ESS_REQUIRE(p.brick >= 2 && p.brick <= 64, "brick must be in 2..64");
+            ESS_REQUIRE(p.nbins == 0 || (p.nbins >= 2 && p.nbins <= 64), "nbins must be 0 or 2..64");
+            ESS_REQUIRE(p.halting == 0 || p.halting == 1, "halting must be 0 or 1");
+            ESS_REQUIRE(p.mls >= 0, "mls must be >= 0");
+            ESS_REQUIRE(p.empty_test == 0 || p.empty_test == 1, "empty_test must be 0 or 1");
+            int B = p.brick;
+            s->gx = (v.nx + B - 1) / B;
+            s->gy = (v.ny + B - 1) / B;
+            s->gz = (v.nz + B - 1) / B;
+            s->nb = (int64_t)s->gx * s->gy * s->gz;
+            size_t nblk = compact_block_count(s->nb);
+            size_t mask_bytes = nblk * 4096;
+            s->mask = (uint8_t *)c.alloc(mask_bytes);
+            ESS_CUDA(cudaMemsetAsync(s->mask, 0, mask_bytes, c.stream));
+            s->ids = (uint32_t *)c.alloc(sizeof(uint32_t) * (size_t)s->nb);
+            s->count = (int *)c.alloc(sizeof(int));
+            s->block_sums = (uint32_t *)c.alloc(sizeof(uint32_t) * nblk);
+            s->block_sums_n = nblk;
+            s->device_bytes = mask_bytes + sizeof(uint32_t) * ((size_t)s->nb + nblk) + sizeof(int);
+        }
+        s->p = p;
+        try {
+            if (kind != ESS_NONE) run_build(c, *s);
+            else s->tf_version = t.version;
+        } catch (...) {
+            free_structure(c, *s);
+            throw;
+        }
+        v.refs++;
+        t.refs++;
+        ess_handle h = new_handle(c, TAG_ST);
+        c.structures[h] = std::move(s);
+        *structure = h;
+    });
+}
+
+ess_status ess_rebuild(ess_ctx *ctx, ess_handle structure)
+{
+    return guard(ctx, [&](Ctx &c) {
+        Structure &s = get_st(c, structure);
+        if (s.kind == ESS_NONE) {
+            s.tf_version = get_tf(c, s.tf).version;
+            return;
+        }
+        run_build(c, s);
+    });
+}
+
+ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_structure_info *info)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(info, "null pointer");
+        Structure &s = get_st(c, structure);
+        std::memset(info, 0, sizeof(*info));
+        info->kind = s.kind;
+        info->brick = s.p.brick;
+        info->gx = s.gx;
+        info->gy = s.gy;
+        info->gz = s.gz;
+        info->n_bricks = s.nb;
+        if (s.kind != ESS_NONE) info->n_nonempty = nonempty_count(c, s);
+        info->n_nodes = 0;
+        info->height = s.kind == ESS_NONE ? 0 : 1;
+        info->device_bytes = s.device_bytes;
+    });
+}
+
+ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array which, void *dst,
+                              size_t capacity, size_t *written)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(dst || capacity == 0, "null destination");
+        Structure &s = get_st(c, structure);
+        ESS_REQUIRE(s.kind != ESS_NONE, "an ESS_NONE structure holds no arrays");
+        int64_t n = nonempty_count(c, s);
+        switch (which) {
+        case ESS_ARR_MINMAX: {
+            ESS_REQUIRE(s.p.empty_test == 0, "min/max is only kept for the range test");
+            Volume &v = get_vol(c, s.vol);
+            copy_out(c, dst, minmax_for(c, v, s.p.brick), sizeof(float2) * s.nb, capacity, written);
+            break;
+        }
+        case ESS_ARR_MASK: copy_out(c, dst, s.mask, (size_t)s.nb, capacity, written); break;
+        case ESS_ARR_IDS: copy_out(c, dst, s.ids, sizeof(uint32_t) * n, capacity, written); break;
+        default: throw Error{ESS_ERR_ARG, "array not available for this structure kind"};
+        }
+    });
+}
+
+ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *camera,
+                      const ess_render_params *params, int W, int H, float *out, int out_on_device)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(camera && params && out, "null pointer");
+        ESS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "image size must be in 1..16384");
+        ESS_REQUIRE(params->dt >= 1e-3f && params->dt <= 1e4f, "dt must be in [1e-3, 1e4]");
+        ESS_REQUIRE(std::isfinite(params->ert), "ert must be finite");
+        for (int i = 0; i < 3; ++i)
+            ESS_REQUIRE(std::isfinite(camera->eye[i]) && std::isfinite(camera->u[i]) &&
+                            std::isfinite(camera->v[i]) && std::isfinite(camera->w[i]),
+                        "camera must be finite");
+        ESS_REQUIRE(camera->w[0] != 0.0f || camera->w[1] != 0.0f || camera->w[2] != 0.0f ||
+                        !camera->ortho,
+                    "orthographic camera needs a non-zero forward vector");
+        Structure &s = get_st(c, structure);
+        Volume &v = get_vol(c, s.vol);
+        TF &t = get_tf(c, s.tf);
+        if (s.tf_version != t.version)
+            throw Error{ESS_ERR_STALE, "structure was built for an older TF table: rebuild it"};
+        RenderJob j;
+        j.vol = &v;
+        j.tf = &t;
+        j.st = &s;
+        j.cam = *camera;
+        j.rp = *params;
+        j.W = W;
+        j.H = H;
+        size_t bytes = (size_t)W * H * 4 * sizeof(float);
+        if (out_on_device) {
+            j.out = out;
+            launch_render(c, j);
+        } else {
+            if (c.stage_bytes < bytes) {
+                c.free(c.stage);
+                c.stage = (float *)c.alloc(bytes);
+                c.stage_bytes = bytes;
+            }
+            j.out = c.stage;
+            launch_render(c, j);
+            ESS_CUDA(cudaMemcpyAsync(out, c.stage, bytes, cudaMemcpyDeviceToHost, c.stream));
+            ESS_CUDA(cudaStreamSynchronize(c.stream));
+        }
+    });
+}
+
+uint64_t ess_launch_count(const ess_ctx *ctx) { return ctx ? ctx->c.launches : 0; }
+
+ess_status ess_sample_count(ess_ctx *ctx, uint64_t *samples, int reset)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(samples, "null pointer");
+        unsigned long long v = 0;
+        ESS_CUDA(cudaMemcpyAsync(&v, c.samples, sizeof(v), cudaMemcpyDeviceToHost, c.stream));
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        *samples = v;
+        if (reset) ESS_CUDA(cudaMemsetAsync(c.samples, 0, sizeof(v), c.stream));
+    });
+}
+
+ess_status ess_profile_enable(ess_ctx *ctx, int enable)
+{
+    return guard(ctx, [&](Ctx &c) { c.profiling = enable != 0; });
+}
+
+ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names, uint64_t *launches,
+                            double *total_ms, int *count)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(count, "null pointer");
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        for (auto &p : c.pending) {
+            float ms = 0.0f;
+            ESS_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+            auto &e = c.prof[p.name];
+            e.first += 1;
+            e.second += ms;
+            c.free_events.push_back(p.a);
+            c.free_events.push_back(p.b);
+        }
+        c.pending.clear();
+        int k = 0;
+        for (auto &kv : c.prof) {
+            if (k < max) {
+                if (names) {
+                    // names are the static literals given at launch sites
+                    names[k] = kv.first.c_str();
+                }
+                if (launches) launches[k] = kv.second.first;
+                if (total_ms) total_ms[k] = kv.second.second;
+            }
+            ++k;
+        }
+        *count = k;
+    });
+}
+
+ess_status ess_profile_reset(ess_ctx *ctx)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        for (auto &p : c.pending) {
+            c.free_events.push_back(p.a);
+            c.free_events.push_back(p.b);
+        }
+        c.pending.clear();
+        c.prof.clear();
+    });
+}
+
+}  // extern "C"

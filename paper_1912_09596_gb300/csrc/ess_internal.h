@@ -1,0 +1,184 @@
+// ess_internal.h -- objects, device layouts and kernel launchers shared by
+// the translation units of libess.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "ess.h"
+
+namespace ess {
+
+// ---------------------------------------------------------------- errors
+// Bits of the device status word that kernels set instead of trapping.
+enum : uint32_t {
+    DEV_ERR_NONFINITE = 1u,  // a float voxel was NaN or infinite
+    DEV_ERR_TIMEOUT = 2u,    // a bounded spin-wait gave up
+    DEV_ERR_OVERFLOW = 4u    // a fixed-capacity device buffer would overflow
+};
+
+struct Error {
+    ess_status st;
+    std::string msg;
+};
+
+#define ESS_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::ess::Error{e_ == cudaErrorMemoryAllocation ? ESS_ERR_OOM        \
+                                                               : ESS_ERR_CUDA,      \
+                               std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+#define ESS_REQUIRE(cond, msg)                                    \
+    do {                                                          \
+        if (!(cond)) throw ::ess::Error{ESS_ERR_ARG, (msg)};      \
+    } while (0)
+
+// ---------------------------------------------------- device-side layouts
+// Node of a binary box tree (LBVH and k-d share it): both children's boxes
+// live in the parent so one 32-byte load feeds both slab tests.  Boxes are in
+// brick coordinates, hi exclusive.  child >= 0: inner node; child < 0: leaf,
+// payload -1 - child (LBVH: brick id; k-d: leaf index).
+struct __align__(16) BoxNode {
+    uint16_t lbox[6];
+    uint16_t rbox[6];
+    int32_t left, right;
+};
+static_assert(sizeof(BoxNode) == 32, "BoxNode must be 32 bytes");
+
+// ------------------------------------------------------------------ objects
+struct Ctx;
+
+struct Volume {
+    int nx, ny, nz;
+    ess_dtype dtype;
+    float value_lo, value_hi;
+    void *data = nullptr;   // device copy, x fastest
+    size_t bytes = 0;
+    std::map<int, float2 *> minmax;  // per brick size: apron min/max (cached)
+    int refs = 0;           // structures using the volume
+    bool released = false;
+};
+
+struct TF {
+    int nt;
+    float4 *table = nullptr;  // device, nt entries
+    int *prefix = nullptr;    // device, nt+1 counts of alpha > 0
+    uint64_t version = 0;     // bumped by every update
+    float *staging = nullptr;       // pinned host copy for asynchronous uploads
+    cudaEvent_t staged = nullptr;   // completion of the last staged upload
+    int refs = 0;
+    bool released = false;
+};
+
+struct Structure {
+    ess_kind kind;
+    ess_build_params p;
+    ess_handle vol = 0, tf = 0;
+    uint64_t tf_version = 0;
+    int gx = 0, gy = 0, gz = 0;
+    int64_t nb = 0;
+    // grid / common
+    uint8_t *mask = nullptr;     // nb (padded)
+    uint32_t *ids = nullptr;     // nb capacity
+    int *count = nullptr;        // device: number of non-empty bricks
+    uint32_t *block_sums = nullptr;
+    size_t block_sums_n = 0;
+    int64_t n_host = -1;         // non-empty count once read back
+    // LBVH
+    uint32_t *keys = nullptr, *keys_alt = nullptr, *ids_sorted = nullptr, *ids_alt = nullptr;
+    uint32_t *sort_scratch = nullptr;
+    size_t sort_scratch_bytes = 0;
+    int32_t *left = nullptr, *right = nullptr, *parent = nullptr, *leaf_parent = nullptr;
+    int32_t *inner_box = nullptr;  // (n-1) x 6
+    int *arrive = nullptr;
+    BoxNode *nodes = nullptr;      // LBVH: n-1 nodes; k-d: inner nodes
+    int32_t root_box[6] = {0, 0, 0, 0, 0, 0};
+    int32_t root_ref = -1;         // root child reference (inner 0 or a leaf)
+    int height = 0;
+    // k-d
+    int32_t *kd_nodes = nullptr;   // max_nodes x 9 (debug / parity layout)
+    int kd_capacity = 0;
+    int64_t kd_count = 0;
+    int32_t *kd_leaf_box = nullptr;  // leaves x 6
+    int32_t *kd_aux = nullptr;       // scratch for the level loop
+    size_t kd_aux_bytes = 0;
+    int *brick_node = nullptr;       // per non-empty brick: current node
+    size_t device_bytes = 0;
+    bool released = false;
+};
+
+// ---------------------------------------------------------------- context
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string last_error;
+    uint64_t next_handle = 1;
+    std::unordered_map<ess_handle, std::unique_ptr<Volume>> volumes;
+    std::unordered_map<ess_handle, std::unique_ptr<TF>> tfs;
+    std::unordered_map<ess_handle, std::unique_ptr<Structure>> structures;
+    uint32_t *dev_status = nullptr;   // device status word
+    uint32_t *host_status = nullptr;  // pinned mirror
+    float *stage = nullptr;           // device image staging for host output
+    size_t stage_bytes = 0;
+    uint64_t launches = 0;
+    unsigned long long *samples = nullptr;  // device: samples evaluated by renders
+    // profiling
+    bool profiling = false;
+    struct Pending { const char *name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    std::map<std::string, std::pair<uint64_t, double>> prof;
+
+    void *alloc(size_t bytes);
+    void free(void *p);
+    void begin(const char *name);   // before a kernel launch
+    void end();                     // after a kernel launch (checks the launch)
+    cudaEvent_t event();
+    const char *current = nullptr;
+    cudaEvent_t cur_a = nullptr;
+};
+
+// Launch bracket: counts the launch, records profiling events and checks the
+// launch error.
+struct Launch {
+    Ctx &c;
+    Launch(Ctx &ctx, const char *name) : c(ctx) { c.begin(name); }
+    ~Launch() noexcept(false) { c.end(); }
+};
+
+// ----------------------------------------------------------- launchers
+// classify.cu
+void launch_check_finite(Ctx &c, const float *v, size_t n);
+void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out);
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix);
+void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf,
+                       float value_lo, float s, uint8_t *mask);
+void launch_brick_mask_cells(Ctx &c, const Volume &v, int B, const TF &tf, float s,
+                             uint8_t *mask, int gx, int gy, int gz);
+size_t compact_block_count(int64_t nb);
+void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int *count,
+                    uint32_t *block_sums);
+
+// render.cu
+struct RenderJob {
+    const Volume *vol;
+    const TF *tf;
+    const Structure *st;
+    ess_camera cam;
+    ess_render_params rp;
+    int W, H;
+    float *out;  // device, W*H*4
+};
+void launch_render(Ctx &c, const RenderJob &job);
+
+}  // namespace ess

@@ -1,0 +1,272 @@
+"""Thin ctypes binding of libess (the C ABI in ``include/ess.h``).
+
+Only argument marshalling happens here: every step of volume upload, empty
+test, structure build and rendering runs in the library's CUDA kernels.  The
+functions keep the C names (``ess_create``, ``ess_volume_upload``, ...); a
+failing call raises :class:`EssError` carrying the status and the library's
+message.  Buffers may be numpy arrays (host) or torch tensors (host or CUDA);
+PyTorch only provides device memory and the CUDA stream.
+
+Importing this module loads ``libess.so`` and fails loudly if it is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libess.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_HANDLE, ERR_TIMEOUT, ERR_BUSY, ERR_STALE = 0, -1, -2, -3, -4, -5, -6, -7
+U8, U16, F32 = 0, 1, 2
+GRID, LBVH, KD, NONE = 0, 1, 2, 3
+KIND_NAMES = {GRID: "grid", LBVH: "lbvh", KD: "kd", NONE: "none"}
+KINDS = (NONE, GRID)   # structure kinds this library builds
+(ARR_MINMAX, ARR_MASK, ARR_IDS, ARR_KEYS, ARR_SORTED_KEYS, ARR_SORTED_IDS, ARR_LBVH_LEFT,
+ ARR_LBVH_RIGHT, ARR_LBVH_BOXES, ARR_KD_NODES) = range(10)
+
+_NP_DTYPE = {np.dtype(np.uint8): U8, np.dtype(np.uint16): U16, np.dtype(np.float32): F32}
+
+
+class EssError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("ess status %d: %s" % (status, message))
+        self.status = status
+        self.message = message
+
+
+class BuildParams(C.Structure):
+    _fields_ = [("brick", C.c_int), ("nbins", C.c_int), ("halting", C.c_int),
+                ("mls", C.c_int), ("empty_test", C.c_int)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("u", C.c_float * 3), ("v", C.c_float * 3),
+                ("w", C.c_float * 3), ("ortho", C.c_int)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4)]
+
+
+class StructureInfo(C.Structure):
+    _fields_ = [("kind", C.c_int), ("brick", C.c_int), ("gx", C.c_int), ("gy", C.c_int),
+                ("gz", C.c_int), ("n_bricks", C.c_int64), ("n_nonempty", C.c_int64),
+                ("n_nodes", C.c_int64), ("height", C.c_int), ("device_bytes", C.c_size_t)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libess.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    vp, i, f, h = C.c_void_p, C.c_int, C.c_float, C.c_uint64
+    P = C.POINTER
+    sigs = {
+        "ess_create": [i, vp, P(vp)],
+        "ess_destroy": [vp],
+        "ess_sync": [vp],
+        "ess_release": [vp, h],
+        "ess_volume_upload": [vp, vp, i, i, i, i, i, f, f, P(h)],
+        "ess_tf_set": [vp, vp, i, i, P(h)],
+        "ess_tf_update": [vp, h, vp, i, i],
+        "ess_build": [vp, h, h, i, P(BuildParams), P(h)],
+        "ess_rebuild": [vp, h],
+        "ess_structure_info_get": [vp, h, P(StructureInfo)],
+        "ess_structure_read": [vp, h, i, vp, C.c_size_t, P(C.c_size_t)],
+        "ess_render": [vp, h, P(Camera), P(RenderParams), i, i, vp, i],
+        "ess_sample_count": [vp, P(C.c_uint64), i],
+        "ess_profile_enable": [vp, i],
+        "ess_profile_read": [vp, i, P(C.c_char_p), P(C.c_uint64), P(C.c_double), P(i)],
+        "ess_profile_reset": [vp],
+    }
+    for name, args in sigs.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = i
+    L.ess_last_error.argtypes = [vp]
+    L.ess_last_error.restype = C.c_char_p
+    L.ess_launch_count.argtypes = [vp]
+    L.ess_launch_count.restype = C.c_uint64
+    return L
+
+
+lib = _load()
+
+
+def _check(ctx, st):
+    if st != OK:
+        msg = lib.ess_last_error(ctx) if ctx else b""
+        raise EssError(st, (msg or b"").decode())
+
+
+def _ptr(buf):
+    """(address, on_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data, 0
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), int(buf.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _dtype_code(buf):
+    if isinstance(buf, np.ndarray):
+        return _NP_DTYPE[buf.dtype]
+    import torch
+    return {torch.uint8: U8, torch.uint16: U16, torch.float32: F32}[buf.dtype]
+
+
+# ------------------------------------------------------------------ the ABI
+def ess_create(device=0, stream=None):
+    """`stream`: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    ctx = C.c_void_p()
+    _check(None, lib.ess_create(device, C.c_void_p(raw) if raw else None, C.byref(ctx)))
+    return ctx
+
+
+def ess_destroy(ctx):
+    _check(None, lib.ess_destroy(ctx))
+
+
+def ess_last_error(ctx):
+    return (lib.ess_last_error(ctx) or b"").decode()
+
+
+def ess_sync(ctx):
+    _check(ctx, lib.ess_sync(ctx))
+
+
+def ess_release(ctx, handle):
+    _check(ctx, lib.ess_release(ctx, handle))
+
+
+def ess_volume_upload(ctx, data, value_lo, value_hi):
+    """`data`: (nz, ny, nx) uint8 / uint16 / float32 array or tensor."""
+    nz, ny, nx = data.shape
+    p, dev = _ptr(data)
+    h = C.c_uint64()
+    _check(ctx, lib.ess_volume_upload(ctx, p, dev, _dtype_code(data), nx, ny, nz,
+                                      float(value_lo), float(value_hi), C.byref(h)))
+    return h.value
+
+
+def ess_tf_set(ctx, rgba):
+    """`rgba`: (nt, 4) float32 array or tensor."""
+    p, dev = _ptr(rgba)
+    h = C.c_uint64()
+    _check(ctx, lib.ess_tf_set(ctx, p, dev, int(rgba.shape[0]), C.byref(h)))
+    return h.value
+
+
+def ess_tf_update(ctx, tf, rgba):
+    p, dev = _ptr(rgba)
+    _check(ctx, lib.ess_tf_update(ctx, tf, p, dev, int(rgba.shape[0])))
+
+
+def build_params(brick=8, nbins=4, halting=1, mls=0, empty_test=0):
+    return BuildParams(brick, nbins, halting, mls, empty_test)
+
+
+def ess_build(ctx, vol, tf, kind, params=None):
+    params = params or build_params()
+    h = C.c_uint64()
+    _check(ctx, lib.ess_build(ctx, vol, tf, kind, C.byref(params), C.byref(h)))
+    return h.value
+
+
+def ess_rebuild(ctx, structure):
+    _check(ctx, lib.ess_rebuild(ctx, structure))
+
+
+def ess_structure_info_get(ctx, structure):
+    info = StructureInfo()
+    _check(ctx, lib.ess_structure_info_get(ctx, structure, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in StructureInfo._fields_}
+
+
+_ARR_DTYPE = {ARR_MINMAX: np.float32, ARR_MASK: np.uint8, ARR_IDS: np.uint32,
+              ARR_KEYS: np.uint32, ARR_SORTED_KEYS: np.uint32, ARR_SORTED_IDS: np.uint32,
+              ARR_LBVH_LEFT: np.int32, ARR_LBVH_RIGHT: np.int32, ARR_LBVH_BOXES: np.int32,
+              ARR_KD_NODES: np.int32}
+
+
+def ess_structure_read(ctx, structure, which, capacity=None):
+    """Returns the array as numpy (1-d; reshape per include/ess.h)."""
+    if capacity is None:
+        info = ess_structure_info_get(ctx, structure)
+        capacity = 16 * max(info["n_bricks"], 9 * info["n_nodes"], 1) + 64
+    buf = np.empty(capacity, dtype=np.uint8)
+    written = C.c_size_t()
+    _check(ctx, lib.ess_structure_read(ctx, structure, which, buf.ctypes.data, capacity,
+                                       C.byref(written)))
+    return buf[: written.value].view(_ARR_DTYPE[which]).copy()
+
+
+def camera(eye, u, v, w, ortho=0):
+    c = Camera()
+    for name, val in (("eye", eye), ("u", u), ("v", v), ("w", w)):
+        for i in range(3):
+            getattr(c, name)[i] = float(val[i])
+    c.ortho = int(ortho)
+    return c
+
+
+def camera_from(cam):
+    """From any object with eye/u/v/w/ortho attributes (e.g. synth.Camera)."""
+    return camera(cam.eye, cam.u, cam.v, cam.w, cam.ortho)
+
+
+def render_params(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0)):
+    p = RenderParams()
+    p.dt = dt
+    p.ert = ert
+    for i in range(4):
+        p.bg[i] = float(bg[i])
+    return p
+
+
+def ess_render(ctx, structure, cam, params, W, H, out):
+    """`out`: (H, W, 4) float32 numpy array (host) or CUDA tensor (device)."""
+    if not isinstance(cam, Camera):
+        cam = camera_from(cam)
+    p, dev = _ptr(out)
+    _check(ctx, lib.ess_render(ctx, structure, C.byref(cam), C.byref(params), W, H, p, dev))
+    return out
+
+
+def ess_launch_count(ctx):
+    return int(lib.ess_launch_count(ctx))
+
+
+def ess_sample_count(ctx, reset=False):
+    v = C.c_uint64()
+    _check(ctx, lib.ess_sample_count(ctx, C.byref(v), int(bool(reset))))
+    return v.value
+
+
+def ess_profile_enable(ctx, enable=True):
+    _check(ctx, lib.ess_profile_enable(ctx, int(bool(enable))))
+
+
+def ess_profile_read(ctx):
+    """{kernel name: (launches, total ms)}"""
+    n = C.c_int()
+    _check(ctx, lib.ess_profile_read(ctx, 0, None, None, None, C.byref(n)))
+    m = n.value
+    names = (C.c_char_p * max(1, m))()
+    launches = (C.c_uint64 * max(1, m))()
+    ms = (C.c_double * max(1, m))()
+    _check(ctx, lib.ess_profile_read(ctx, m, names, launches, ms, C.byref(n)))
+    return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(m)}
+
+
+def ess_profile_reset(ctx):
+    _check(ctx, lib.ess_profile_reset(ctx))

@@ -18,3 +18,23 @@ def ora():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """(ess binding, torch) with a context on cuda:0; skips without a GPU."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09596_gb300 import ess
+    return ess, torch
+
+
+@pytest.fixture()
+def ctx(gpu):
+    ess, torch = gpu
+    c = ess.ess_create(0, torch.cuda.current_stream())
+    yield c
+    ess.ess_destroy(c)
