@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the empty-space-skipping hot path on one GB300 (per rank).
+
+A step is one pass of the whole hot path over the 512^3 CT-like workload:
+for each of 8 transfer-function edits, the TF table is replaced, every
+skipping structure (macrocell grid, LBVH, k-d tree) is rebuilt from it and a
+1024 x 1024 frame is rendered through each structure (dt 0.5, early ray
+termination at opacity 0.99; the camera rotates by 45 degrees per edit).
+
+value: ray samples per second, counting for every frame the samples the naive
+       (non-skipping) marcher takes for that frame, i.e. the work each image
+       stands for; the time covers TF upload, rebuilds and renders, with all
+       inputs resident in device memory.  The samples the skipping renderers
+       actually evaluate are reported beside it.
+e2e:   the same metric through the C ABI with host buffers: TF tables copied
+       from pinned host memory and every frame read back to pinned host memory
+       inside the timed region.
+
+`--impl reference` times the CPU oracle (the plain definition: naive marcher)
+on the same workload instead; under torchrun only rank 0 runs it.
+
+Multi-GPU: the path does not shard; N ranks run N independent replicas (weak
+scaling), timed between barriers with the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ct512": dict(
+        desc="512^3 uint8 CT-like volume (noisy shells, vessels, 2% smooth noise); "
+             "8 TF edits with 5-30% non-empty 8^3 bricks; rebuild per edit; "
+             "1024x1024 perspective, dt 0.5 voxel, ERT 0.99",
+        dims=(512, 512, 512), W=1024, H=1024, dt=0.5, ert=0.99, brick=8),
+    "blobs64": dict(
+        desc="64^3 uint8 Gaussian blobs, TF ramp from 40, brick 8^3, 256x256 perspective, "
+             "dt 0.5, no ERT", dims=(64, 64, 64), W=256, H=256, dt=0.5, ert=2.0, brick=8),
+}
+KD_PARAMS = dict(nbins=4, halting=1, mls=32)   # GPU k-d, deep, maximum leaf 32^3 (Sec. 4.3)
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def make_inputs(name):
+    from paper_1912_09596_gb300 import synth
+    w = WORKLOADS[name]
+    if name == "ct512":
+        vol = synth.ct_like_u8(w["dims"], seed=1)
+        tfs = synth.tf_set_ct(256)
+    else:
+        vol = synth.blobs_u8(w["dims"], seed=0)
+        tfs = [synth.tf_ramp(256, 40) for _ in range(8)]
+    cams = [synth.orbit_camera(w["dims"], w["W"], w["H"], theta=2 * math.pi * i / len(tfs),
+                               phi=0.35, dist=1.6) for i in range(len(tfs))]
+    return vol, (0.0, 255.0), tfs, cams
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.lines = []
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--id=%d" % device, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1912_09596_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """dram bytes per launch recorded by an ncu capture (profiles/traffic.txt),
+    valid only if the kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload \
+                and f[3] == sha:
+            return float(f[2])
+    return None
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    return rank, local, ws, dist
+
+
+# ---------------------------------------------------------------- reference
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(vol_np, vlo, vhi, tf_np, cam, w, budget_s, threads):
+    """Naive CPU marcher (the oracle) on a stripe of rows of one frame, sized
+    to about `budget_s` seconds.  Returns (samples/s, description)."""
+    import oracle
+    ov, ot = oracle.OVolume(vol_np, vlo, vhi), oracle.OTF(tf_np)
+    W, H = w["W"], w["H"]
+    y0 = H // 2 - 2
+    t0 = time.perf_counter()
+    _, n0 = oracle.render_naive(ov, ot, cam, W, H, dt=w["dt"], ert=w["ert"], rows=(y0, y0 + 4),
+                                threads=threads)
+    probe = time.perf_counter() - t0
+    rows = int(max(4, min(H, 4 * budget_s / max(probe, 1e-3))))
+    ya = max(0, H // 2 - rows // 2)
+    yb = min(H, ya + rows)
+    t0 = time.perf_counter()
+    _, n = oracle.render_naive(ov, ot, cam, W, H, dt=w["dt"], ert=w["ert"], rows=(ya, yb),
+                               threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, "rows %d..%d of a %dx%d frame (%d samples, %.1f s, %d threads)" % (
+        ya, yb, W, H, n, dt, threads)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    vol, (vlo, vhi), tfs, cams = make_inputs(args.workload)
+    cores = cpu_cores()
+    for _ in range(args.warmup):
+        oracle_rate(vol, vlo, vhi, tfs[0], cams[0], w, 0.2, cores)
+    rates, descs, t_all = [], [], 0.0
+    for k in range(args.steps):
+        i = k % len(tfs)
+        t0 = time.perf_counter()
+        r, d = oracle_rate(vol, vlo, vhi, tfs[i], cams[i], w, args.ref_budget, cores)
+        t_all += time.perf_counter() - t0
+        rates.append(r)
+        descs.append(d)
+    value = float(statistics.mean(rates))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_all / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + w["desc"]},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: " + descs[0]},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+METRIC = ("ray samples/s (naive-equivalent) over TF edit + rebuild + render of grid, "
+          "LBVH and k-d structures")
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, rank, local, ws, dist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_09596_gb300 import ess
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    vol_np, (vlo, vhi), tfs_np, cams = make_inputs(args.workload)
+    W, H, B = w["W"], w["H"], w["brick"]
+    stream = torch.cuda.Stream(device=dev)
+    kinds = [k for k in ess.KINDS if k != ess.NONE]
+
+    with torch.cuda.stream(stream):
+        ctx = ess.ess_create(local, stream)
+        vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).to(dev), vlo, vhi)
+        tf_dev = [torch.from_numpy(t).to(dev) for t in tfs_np]
+        tf_host = [torch.from_numpy(t).pin_memory() for t in tfs_np]
+        tf = ess.ess_tf_set(ctx, tf_dev[0])
+        params = {k: ess.build_params(brick=B, **KD_PARAMS) for k in kinds}
+        st = {k: ess.ess_build(ctx, vol, tf, k, params[k]) for k in kinds}
+        naive = ess.ess_build(ctx, vol, tf, ess.NONE)
+        outs = {k: torch.empty((H, W, 4), dtype=torch.float32, device=dev) for k in kinds}
+        host_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        rp = ess.render_params(w["dt"], w["ert"])
+        ecams = [ess.camera_from(c) for c in cams]
+
+        # per-edit reference counts (untimed): naive samples, evaluated samples,
+        # non-empty bricks, algorithmic bytes of each render
+        n_naive, n_eval, alg_bytes, nonempty = [], {k: [] for k in kinds}, {k: [] for k in kinds}, []
+        for i in range(len(tfs_np)):
+            ess.ess_tf_update(ctx, tf, tf_dev[i])
+            ess.ess_rebuild(ctx, naive)
+            ess.ess_sample_count(ctx, reset=True)
+            ess.ess_render(ctx, naive, ecams[i], rp, W, H, outs[kinds[0]])
+            n_naive.append(ess.ess_sample_count(ctx, reset=True))
+            for k in kinds:
+                ess.ess_rebuild(ctx, st[k])
+                ess.ess_render(ctx, st[k], ecams[i], rp, W, H, outs[k])
+                n_eval[k].append(ess.ess_sample_count(ctx, reset=True))
+                info = ess.ess_structure_info_get(ctx, st[k])
+                nb = info["n_nonempty"]
+                if k == kinds[0]:
+                    nonempty.append(nb / max(1, info["n_bricks"]))
+                # compulsory bytes of one frame: the image, the voxels of the
+                # non-empty bricks and the structure itself
+                struct_b = info["n_bricks"] if k == ess.GRID else 32 * max(1, info["n_nodes"])
+                alg_bytes[k].append(W * H * 16 + nb * B ** 3 * vol_np.itemsize + struct_b)
+        ess.ess_sync(ctx)
+
+        def step(host_io=False):
+            for i in range(len(tfs_np)):
+                ess.ess_tf_update(ctx, tf, tf_host[i] if host_io else tf_dev[i])
+                for k in kinds:
+                    ess.ess_rebuild(ctx, st[k])
+                    ess.ess_render(ctx, st[k], ecams[i], rp, W, H, host_out if host_io else outs[k])
+
+        for _ in range(args.warmup):
+            step()
+        ess.ess_sync(ctx)
+        launches0 = ess.ess_launch_count(ctx)
+        ess.ess_profile_reset(ctx)
+        ess.ess_profile_enable(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local)
+        for s in range(args.steps):
+            flush.zero_()                        # L2 flush between timed steps (untimed)
+            ev[s][0].record(stream)
+            step()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        launches = ess.ess_launch_count(ctx) - launches0
+        ess.ess_profile_enable(ctx, False)
+        prof = ess.ess_profile_read(ctx)
+        ess.ess_sync(ctx)
+        t_ms = sum(a.elapsed_time(b) for a, b in ev)
+        if dist:
+            tt = torch.tensor([t_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_ms = float(tt.item())
+
+        # end to end through the ABI with host buffers
+        for _ in range(max(1, args.warmup // 2)):
+            step(host_io=True)
+        ess.ess_sync(ctx)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(host_io=True)
+        ess.ess_sync(ctx)
+        e2e_ms = 1000.0 * (time.perf_counter() - t0)
+        if dist:
+            tt = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt.item())
+
+    units_step = sum(n_naive) * len(kinds)
+    evaluated_step = sum(sum(v) for v in n_eval.values())
+    value = ws * units_step * args.steps / (t_ms / 1000.0)
+    e2e_value = ws * units_step * args.steps / (e2e_ms / 1000.0)
+
+    # dominant kernel and its roofline on algorithmic bytes
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    avg_ms = dom_ms / max(1, dom_launches)
+    kind_of = {"render_grid": ess.GRID, "render_lbvh": ess.LBVH, "render_kd": ess.KD}
+    peak, peak_src = measured_peaks()
+    if dom_name in kind_of and kind_of[dom_name] in alg_bytes:
+        bytes_per_launch = float(np.mean(alg_bytes[kind_of[dom_name]]))
+    else:
+        bytes_per_launch = None
+    roof = None
+    if bytes_per_launch is not None:
+        achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dom_name, args.workload),
+                "kernel": dom_name, "avg_launch_ms": avg_ms,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_src}
+
+    per_frame = {}
+    build_ms = {}
+    for name, (n, ms) in prof.items():
+        for kname, k in kind_of.items():
+            if name == kname:
+                per_frame[ess.KIND_NAMES[k]] = ms / max(1, n)
+    build_kernels = {nm: v for nm, v in prof.items() if not nm.startswith("render")}
+    total_build_ms = sum(v[1] for v in build_kernels.values())
+    edits = args.steps * len(tfs_np)
+    build_ms["all_structures_per_edit"] = total_build_ms / edits
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": " + w["desc"],
+                   "structures": [ess.KIND_NAMES[k] for k in kinds],
+                   "kd": KD_PARAMS, "brick": B, "image": "%dx%d" % (W, H),
+                   "tf_edits_per_step": len(tfs_np),
+                   "nonempty_brick_fraction": [round(x, 4) for x in nonempty],
+                   "l2": "flushed between timed steps (%d MiB write, untimed)" % (L2_FLUSH_BYTES >> 20),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "evaluated_samples_per_s": ws * evaluated_step * args.steps / (t_ms / 1000.0),
+        "ms_per_frame": per_frame,
+        "build_ms_per_edit": build_ms,
+        "kernel_ms": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "samples/s",
+                "h2d_bytes_per_step": int(sum(t.numel() * 4 for t in tf_host)),
+                "d2h_bytes_per_step": int(len(tfs_np) * len(kinds) * W * H * 16),
+                "ms_per_step": e2e_ms / args.steps},
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        rate, desc = oracle_rate(vol_np, vlo, vhi, tfs_np[0], cams[0], w, args.ref_budget, cores)
+        result["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": cores,
+                                  "kind": "oracle", "sample": desc}
+    with torch.cuda.stream(stream):
+        ess.ess_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ct512")
+    ap.add_argument("--ref-budget", type=float, default=6.0,
+                    help="seconds of oracle work per CPU measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, local, ws, dist = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if dist:
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, local, ws, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -101,7 +101,9 @@ ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
 /* Sets an RGBA transfer function of `nt` entries (Sec. 1: the colour and
  * alpha TF that maps scalar values to colour and opacity), `rgba` = nt*4
  * floats, entry-major.  Alpha must lie in [0, 1] and every value must be
- * finite.  2 <= nt <= 65536.  Copies the table. */
+ * finite, 2 <= nt <= 65536.  Copies the table.  A host table is checked
+ * before the call returns (ESS_ERR_ARG); a device table is checked on the
+ * device and a bad one is reported by the next ess_sync (ESS_ERR_ARG). */
 ess_status ess_tf_set(ess_ctx *ctx, const float *rgba, int on_device, int nt,
                       ess_handle *tf);
 

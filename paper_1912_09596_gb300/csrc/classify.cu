@@ -98,16 +98,26 @@ void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out)
 }
 
 // --------------------------------------------------------- K2 TF prefix
-// prefix[i] = #{j < i : alpha_j > 0}, i = 0..nt (one block).
+// prefix[i] = #{j < i : alpha_j > 0}, i = 0..nt (one block).  With
+// `validate`, a table that holds a non-finite value or an alpha outside
+// [0, 1] sets DEV_ERR_BAD_TF (tables uploaded from device memory are checked
+// here so that a TF edit never waits for the host).
 __global__ void __launch_bounds__(1024) k_tf_prefix(const float4 *__restrict__ table, int nt,
-                                                    int *__restrict__ prefix)
+                                                    int *__restrict__ prefix, int validate,
+                                                    uint32_t *status)
 {
     __shared__ int warp_tot[32];
     int t = threadIdx.x;
     int per = (nt + 1023) / 1024;
     int b0 = t * per, b1 = min(nt, b0 + per);
     int cnt = 0;
-    for (int i = b0; i < b1; ++i) cnt += table[i].w > 0.0f ? 1 : 0;
+    bool bad = false;
+    for (int i = b0; i < b1; ++i) {
+        float4 e = table[i];
+        cnt += e.w > 0.0f ? 1 : 0;
+        bad |= !(isfinite(e.x) && isfinite(e.y) && isfinite(e.z) && e.w >= 0.0f && e.w <= 1.0f);
+    }
+    if (validate && __syncthreads_or(bad) && t == 0) atomicOr(status, DEV_ERR_BAD_TF);
     // block-wide exclusive scan of cnt
     int lane = t & 31, w = t >> 5;
     int incl = cnt;
@@ -134,10 +144,10 @@ __global__ void __launch_bounds__(1024) k_tf_prefix(const float4 *__restrict__ t
     if (t == 1023) prefix[nt] = warp_tot[31];
 }
 
-void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix)
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, int validate)
 {
     Launch L(c, "tf_prefix");
-    k_tf_prefix<<<1, 1024, 0, c.stream>>>(table, nt, prefix);
+    k_tf_prefix<<<1, 1024, 0, c.stream>>>(table, nt, prefix, validate, c.dev_status);
 }
 
 // ---------------------------------------------------- K2 range test (mask)
@@ -339,9 +349,23 @@ __global__ void __launch_bounds__(1024) k_compact_scan(uint32_t *__restrict__ bl
     if (threadIdx.x == 0) *count = carry;
 }
 
+// 30-bit Morton code (Sec. 3.1), bit i of x/y/z at bit 3i/3i+1/3i+2: each
+// 10-bit coordinate is spread to every third bit by shift-and-mask steps.
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
 __global__ void __launch_bounds__(CT_THREADS) k_compact_scatter(const uint8_t *__restrict__ mask,
                                                                 const uint32_t *__restrict__ block_sums,
-                                                                int64_t nb, uint32_t *__restrict__ ids)
+                                                                int64_t nb, uint32_t *__restrict__ ids,
+                                                                uint32_t *__restrict__ keys, int gx,
+                                                                int gy)
 {
     const uint4 *m = reinterpret_cast<const uint4 *>(mask) + (size_t)blockIdx.x * CT_THREADS;
     uint4 v = m[threadIdx.x];
@@ -355,14 +379,21 @@ __global__ void __launch_bounds__(CT_THREADS) k_compact_scatter(const uint8_t *_
     for (int j = 0; j < CT_ITEMS; ++j) {
         if ((w[j >> 2] >> (8 * (j & 3))) & 0xffu) {
             int64_t b = first + j;
-            if (b < nb) ids[off] = (uint32_t)b;
+            if (b < nb) {
+                ids[off] = (uint32_t)b;
+                if (keys) {
+                    uint32_t bx = (uint32_t)(b % gx), by = (uint32_t)((b / gx) % gy);
+                    uint32_t bz = (uint32_t)(b / ((int64_t)gx * gy));
+                    keys[off] = spread3(bx) | (spread3(by) << 1) | (spread3(bz) << 2);
+                }
+            }
             ++off;
         }
     }
 }
 
 void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int *count,
-                    uint32_t *block_sums)
+                    uint32_t *block_sums, uint32_t *morton_keys, int gx, int gy)
 {
     unsigned nblk = (unsigned)compact_block_count(nb);
     {
@@ -375,7 +406,8 @@ void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int 
     }
     {
         Launch L(c, "compact_scatter");
-        k_compact_scatter<<<nblk, CT_THREADS, 0, c.stream>>>(mask, block_sums, nb, ids);
+        k_compact_scatter<<<nblk, CT_THREADS, 0, c.stream>>>(mask, block_sums, nb, ids,
+                                                             morton_keys, gx, gy);
     }
 }
 

@@ -145,6 +145,10 @@ ess_status take_status(Ctx &c, std::string &msg)
         msg = "a device buffer reached its capacity";
         return ESS_ERR_ARG;
     }
+    if (s & DEV_ERR_BAD_TF) {
+        msg = "a TF table from device memory held a non-finite value or an alpha outside [0, 1]";
+        return ESS_ERR_ARG;
+    }
     msg = "volume holds a NaN or infinite value";
     return ESS_ERR_ARG;
 }
@@ -159,33 +163,26 @@ void check_tf_host(const float *rgba, int nt)
     }
 }
 
-// Copies a TF table (host or device) into `t`, validating it on the host.
+// Copies a TF table into `t` and recomputes its prefix counts.  A host table
+// is validated on the host and staged through pinned memory (the caller's
+// buffer is free on return and the copy stays asynchronous); a device table is
+// copied device to device and validated by the prefix kernel, which reports a
+// bad table at the next ess_sync.
 void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
 {
-    std::vector<float> h((size_t)t.nt * 4);
+    size_t bytes = (size_t)t.nt * 4 * sizeof(float);
     if (on_device) {
-        ESS_CUDA(cudaMemcpyAsync(h.data(), rgba, h.size() * sizeof(float), cudaMemcpyDeviceToHost,
-                                 c.stream));
-        ESS_CUDA(cudaStreamSynchronize(c.stream));
+        ESS_CUDA(cudaMemcpyAsync(t.table, rgba, bytes, cudaMemcpyDeviceToDevice, c.stream));
     } else {
-        std::memcpy(h.data(), rgba, h.size() * sizeof(float));
-    }
-    check_tf_host(h.data(), t.nt);
-    if (on_device) {
-        ESS_CUDA(cudaMemcpyAsync(t.table, rgba, h.size() * sizeof(float), cudaMemcpyDeviceToDevice,
-                                 c.stream));
-    } else {
-        // pinned staging so that the copy is truly asynchronous and the caller's
-        // buffer is free on return
-        if (!t.staging) ESS_CUDA(cudaMallocHost(&t.staging, h.size() * sizeof(float)));
+        check_tf_host(rgba, t.nt);
+        if (!t.staging) ESS_CUDA(cudaMallocHost(&t.staging, bytes));
         if (t.staged) ESS_CUDA(cudaEventSynchronize(t.staged));
-        std::memcpy(t.staging, h.data(), h.size() * sizeof(float));
-        ESS_CUDA(cudaMemcpyAsync(t.table, t.staging, h.size() * sizeof(float),
-                                 cudaMemcpyHostToDevice, c.stream));
+        std::memcpy(t.staging, rgba, bytes);
+        ESS_CUDA(cudaMemcpyAsync(t.table, t.staging, bytes, cudaMemcpyHostToDevice, c.stream));
         if (!t.staged) ESS_CUDA(cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
         ESS_CUDA(cudaEventRecord(t.staged, c.stream));
     }
-    launch_tf_prefix(c, t.table, t.nt, t.prefix);
+    launch_tf_prefix(c, t.table, t.nt, t.prefix, on_device);
     ++t.version;
 }
 
@@ -202,11 +199,38 @@ float2 *minmax_for(Ctx &c, Volume &v, int B)
 
 void free_structure(Ctx &c, Structure &s)
 {
-    void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_alt, s.ids_sorted,
-                    s.ids_alt, s.sort_scratch, s.left, s.right, s.parent, s.leaf_parent,
-                    s.inner_box, s.arrive, s.nodes, s.kd_nodes, s.kd_leaf_box, s.kd_aux,
-                    s.brick_node};
+    void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_sorted, s.ids_sorted,
+                    s.keys_alt, s.ids_alt, s.sort_scratch, s.left, s.right, s.parent,
+                    s.leaf_parent, s.inner_box, s.arrive, s.nodes, s.root, s.kd_nodes,
+                    s.kd_leaf_box, s.kd_count_dev, s.kd_aux, s.brick_node};
     for (void *p : ptrs) c.free(p);
+}
+
+template <typename P> P *alloc_n(Ctx &c, Structure &s, size_t n)
+{
+    size_t bytes = sizeof(P) * (n ? n : 1);
+    s.device_bytes += bytes;
+    return (P *)c.alloc(bytes);
+}
+
+// Device buffers of an LBVH over up to nb bricks (Sec. 3.1).
+void alloc_lbvh(Ctx &c, Structure &s)
+{
+    size_t cap = (size_t)s.nb, inner = cap > 1 ? cap - 1 : 1;
+    s.keys = alloc_n<uint32_t>(c, s, cap);
+    s.keys_sorted = alloc_n<uint32_t>(c, s, cap);
+    s.ids_sorted = alloc_n<uint32_t>(c, s, cap);
+    s.keys_alt = alloc_n<uint32_t>(c, s, cap);
+    s.ids_alt = alloc_n<uint32_t>(c, s, cap);
+    s.sort_scratch = alloc_n<uint32_t>(c, s, sort_scratch_words(s.nb));
+    s.left = alloc_n<int32_t>(c, s, inner);
+    s.right = alloc_n<int32_t>(c, s, inner);
+    s.parent = alloc_n<int32_t>(c, s, inner);
+    s.leaf_parent = alloc_n<int32_t>(c, s, cap);
+    s.inner_box = alloc_n<int32_t>(c, s, 6 * inner);
+    s.arrive = alloc_n<int>(c, s, inner);
+    s.nodes = alloc_n<BoxNode>(c, s, inner);
+    s.root = alloc_n<int32_t>(c, s, 8);
 }
 
 // The empty test and compaction (Sec. 3.1), then the kind-specific build.
@@ -222,8 +246,11 @@ void run_build(Ctx &c, Structure &s)
         float2 *mm = minmax_for(c, v, B);
         launch_brick_mask(c, mm, s.nb, t, v.value_lo, sc, s.mask);
     }
-    launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums);
+    launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums,
+                   s.kind == ESS_LBVH ? s.keys : nullptr, s.gx, s.gy);
+    if (s.kind == ESS_LBVH) launch_lbvh(c, s);
     s.n_host = -1;
+    s.height = -1;
     s.tf_version = t.version;
 }
 
@@ -437,7 +464,7 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         ESS_REQUIRE(structure, "null pointer");
         Volume &v = get_vol(c, vol);
         TF &t = get_tf(c, tf);
-        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_NONE,
+        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_NONE,
                     "structure kind not available in this build");
         ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0};
         auto s = std::make_unique<Structure>();
@@ -464,6 +491,16 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
             s->block_sums = (uint32_t *)c.alloc(sizeof(uint32_t) * nblk);
             s->block_sums_n = nblk;
             s->device_bytes = mask_bytes + sizeof(uint32_t) * ((size_t)s->nb + nblk) + sizeof(int);
+            if (kind == ESS_LBVH) {
+                ESS_REQUIRE(s->gx <= 1024 && s->gy <= 1024 && s->gz <= 1024,
+                            "LBVH: at most 1024 bricks per axis (30-bit Morton codes)");
+                try {
+                    alloc_lbvh(c, *s);
+                } catch (...) {
+                    free_structure(c, *s);
+                    throw;
+                }
+            }
         }
         s->p = p;
         try {
@@ -508,6 +545,12 @@ ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_struct
         if (s.kind != ESS_NONE) info->n_nonempty = nonempty_count(c, s);
         info->n_nodes = 0;
         info->height = s.kind == ESS_NONE ? 0 : 1;
+        if (s.kind == ESS_LBVH) {
+            int64_t n = info->n_nonempty;
+            info->n_nodes = n > 0 ? 2 * n - 1 : 0;
+            if (s.height < 0) s.height = n > 0 ? lbvh_height(c, s) : 0;
+            info->height = s.height;
+        }
         info->device_bytes = s.device_bytes;
     });
 }
@@ -529,6 +572,26 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
         }
         case ESS_ARR_MASK: copy_out(c, dst, s.mask, (size_t)s.nb, capacity, written); break;
         case ESS_ARR_IDS: copy_out(c, dst, s.ids, sizeof(uint32_t) * n, capacity, written); break;
+        case ESS_ARR_KEYS:
+        case ESS_ARR_SORTED_KEYS:
+        case ESS_ARR_SORTED_IDS:
+        case ESS_ARR_LBVH_LEFT:
+        case ESS_ARR_LBVH_RIGHT:
+        case ESS_ARR_LBVH_BOXES: {
+            ESS_REQUIRE(s.kind == ESS_LBVH, "array only exists for an LBVH");
+            size_t inner = n > 1 ? (size_t)(n - 1) : 0;
+            const void *src = which == ESS_ARR_KEYS          ? (const void *)s.keys
+                              : which == ESS_ARR_SORTED_KEYS ? (const void *)s.keys_sorted
+                              : which == ESS_ARR_SORTED_IDS  ? (const void *)s.ids_sorted
+                              : which == ESS_ARR_LBVH_LEFT   ? (const void *)s.left
+                              : which == ESS_ARR_LBVH_RIGHT  ? (const void *)s.right
+                                                             : (const void *)s.inner_box;
+            size_t bytes = which <= ESS_ARR_SORTED_IDS ? sizeof(uint32_t) * (size_t)n
+                           : which == ESS_ARR_LBVH_BOXES ? sizeof(int32_t) * 6 * inner
+                                                         : sizeof(int32_t) * inner;
+            copy_out(c, dst, src, bytes, capacity, written);
+            break;
+        }
         default: throw Error{ESS_ERR_ARG, "array not available for this structure kind"};
         }
     });

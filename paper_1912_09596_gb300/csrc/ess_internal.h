@@ -20,7 +20,8 @@ namespace ess {
 enum : uint32_t {
     DEV_ERR_NONFINITE = 1u,  // a float voxel was NaN or infinite
     DEV_ERR_TIMEOUT = 2u,    // a bounded spin-wait gave up
-    DEV_ERR_OVERFLOW = 4u    // a fixed-capacity device buffer would overflow
+    DEV_ERR_OVERFLOW = 4u,   // a fixed-capacity device buffer would overflow
+    DEV_ERR_BAD_TF = 8u      // a device TF table held a non-finite value or alpha outside [0,1]
 };
 
 struct Error {
@@ -94,21 +95,22 @@ struct Structure {
     size_t block_sums_n = 0;
     int64_t n_host = -1;         // non-empty count once read back
     // LBVH
-    uint32_t *keys = nullptr, *keys_alt = nullptr, *ids_sorted = nullptr, *ids_alt = nullptr;
+    uint32_t *keys = nullptr;                                 // Morton code of ids[i]
+    uint32_t *keys_sorted = nullptr, *ids_sorted = nullptr;   // sort result
+    uint32_t *keys_alt = nullptr, *ids_alt = nullptr;         // sort ping-pong
     uint32_t *sort_scratch = nullptr;
-    size_t sort_scratch_bytes = 0;
     int32_t *left = nullptr, *right = nullptr, *parent = nullptr, *leaf_parent = nullptr;
     int32_t *inner_box = nullptr;  // (n-1) x 6
     int *arrive = nullptr;
-    BoxNode *nodes = nullptr;      // LBVH: n-1 nodes; k-d: inner nodes
-    int32_t root_box[6] = {0, 0, 0, 0, 0, 0};
-    int32_t root_ref = -1;         // root child reference (inner 0 or a leaf)
+    BoxNode *nodes = nullptr;      // traversal nodes (LBVH: n-1; k-d: inner nodes)
+    int32_t *root = nullptr;       // device root record: ref, box lo xyz, hi xyz, pad
     int height = 0;
     // k-d
     int32_t *kd_nodes = nullptr;   // max_nodes x 9 (debug / parity layout)
     int kd_capacity = 0;
     int64_t kd_count = 0;
-    int32_t *kd_leaf_box = nullptr;  // leaves x 6
+    int16_t *kd_leaf_box = nullptr;  // leaves x 6 (brick coordinates)
+    int *kd_count_dev = nullptr;     // device: k-d node count
     int32_t *kd_aux = nullptr;       // scratch for the level loop
     size_t kd_aux_bytes = 0;
     int *brick_node = nullptr;       // per non-empty brick: current node
@@ -160,14 +162,22 @@ struct Launch {
 // classify.cu
 void launch_check_finite(Ctx &c, const float *v, size_t n);
 void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out);
-void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix);
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, int validate);
 void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf,
                        float value_lo, float s, uint8_t *mask);
 void launch_brick_mask_cells(Ctx &c, const Volume &v, int B, const TF &tf, float s,
                              uint8_t *mask, int gx, int gy, int gz);
 size_t compact_block_count(int64_t nb);
 void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int *count,
-                    uint32_t *block_sums);
+                    uint32_t *block_sums, uint32_t *morton_keys, int gx, int gy);
+
+// lbvh.cu
+size_t sort_scratch_words(int64_t cap);
+int launch_radix_sort(Ctx &c, const uint32_t *keys, const uint32_t *vals, uint32_t *keys_a,
+                      uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const int *count,
+                      int64_t cap, int bits, uint32_t *scratch);
+void launch_lbvh(Ctx &c, Structure &s);
+int lbvh_height(Ctx &c, Structure &s);
 
 // render.cu
 struct RenderJob {

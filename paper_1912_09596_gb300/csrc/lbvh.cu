@@ -1,0 +1,411 @@
+// lbvh.cu -- LBVH over the non-empty bricks (Sec. 3.1): 30-bit Morton codes
+// (computed in the compaction scatter), a onesweep LSD radix sort of
+// (code, brick id) pairs, Karras' per-node hierarchy emission and a bottom-up
+// pass that assembles the inner-node boxes and the traversal nodes.
+//
+// The non-empty count n lives in device memory; kernels read it there and
+// grids are sized for the brick capacity, so a rebuild needs no host round
+// trip.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+#include "ess_internal.h"
+
+namespace ess {
+
+// ------------------------------------------------------------ K5 onesweep
+// LSD radix sort, 8-bit digits.  One kernel builds the digit histograms of
+// all passes at once; one block scans them into global digit offsets; then
+// one kernel per pass ranks a tile of RS_TILE items stably in shared memory,
+// publishes the tile's per-digit counts and resolves its prefix by decoupled
+// look-back over earlier tiles (tile ids come from an atomic counter, so every
+// earlier tile has already started), and scatters.  Waits on earlier tiles are
+// bounded: after RS_SPIN_LIMIT polls the kernel records DEV_ERR_TIMEOUT and
+// carries on with what it has; scatter positions are bounds-checked, so a
+// timed-out sort returns a wrong order (reported by ess_sync) but never
+// writes outside the buffers.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+constexpr int RS_RADIX = 256;
+constexpr uint32_t RS_FLAG_AGG = 1u << 30, RS_FLAG_INC = 2u << 30, RS_MASK = (1u << 30) - 1;
+constexpr long RS_SPIN_LIMIT = 1L << 22;
+
+size_t sort_tiles(int64_t cap) { return (size_t)((cap + RS_TILE - 1) / RS_TILE); }
+
+size_t sort_scratch_words(int64_t cap)
+{
+    // histograms (4 x 256) + tile counters (4) + tile status (4 x tiles x 256)
+    return 4 * RS_RADIX + 4 + 4 * sort_tiles(cap) * RS_RADIX;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t *__restrict__ keys,
+                                                        const int *__restrict__ count, int passes,
+                                                        uint32_t *__restrict__ ghist)
+{
+    __shared__ uint32_t h[4][RS_RADIX];
+    for (int i = threadIdx.x; i < 4 * RS_RADIX; i += RS_THREADS) (&h[0][0])[i] = 0;
+    __syncthreads();
+    int n = *count;
+    for (int i = blockIdx.x * RS_THREADS + threadIdx.x; i < n; i += gridDim.x * RS_THREADS) {
+        uint32_t k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RS_RADIX; i += RS_THREADS) {
+        uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(ghist + i, v);
+    }
+}
+
+// exclusive scan of each pass's 256 bins: 4 x 256 threads
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ ghist)
+{
+    __shared__ uint32_t wsum[32];
+    int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t v = ghist[t];
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    // 8 warps per pass
+    int p0 = (w >> 3) << 3;
+    uint32_t before = 0;
+    for (int j = p0; j < w; ++j) before += wsum[j];
+    ghist[t] = before + incl - v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_pass(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const int *__restrict__ count, int shift,
+    const uint32_t *__restrict__ offsets, uint32_t *tile_status, uint32_t *tile_counter,
+    uint32_t *status)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_cnt[RS_RADIX];
+    __shared__ uint32_t s_warp[RS_THREADS / 32][RS_RADIX];
+    __shared__ uint32_t s_base[RS_RADIX];
+    const int t = threadIdx.x, w = t >> 5;
+    if (t == 0) s_tile = atomicAdd(tile_counter, 1u);
+    s_cnt[t] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int n = *count;
+    const int64_t base = (int64_t)tile * RS_TILE;
+    if (base >= n) return;  // uniform per block
+
+    uint32_t key[RS_ITEMS], val[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t i = base + r * RS_THREADS + t;
+        bool ok = i < n;
+        key[r] = ok ? kin[i] : 0u;
+        val[r] = ok ? vin[i] : 0u;
+    }
+    // stable ranking, one round of 256 consecutive items at a time
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        bool ok = base + r * RS_THREADS + t < n;
+        uint32_t d = ok ? (key[r] >> shift) & 0xffu : RS_RADIX;  // invalid: own group
+        for (int i = t; i < (RS_THREADS / 32) * RS_RADIX; i += RS_THREADS) (&s_warp[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t below = peers & lanemask_lt();
+        if (ok && below == 0) s_warp[w][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t pre = 0;
+            for (int j = 0; j < w; ++j) pre += s_warp[j][d];
+            rank[r] = s_cnt[d] + pre + __popc(below);
+        }
+        __syncthreads();
+        {
+            uint32_t add = 0;
+#pragma unroll
+            for (int j = 0; j < RS_THREADS / 32; ++j) add += s_warp[j][t];
+            s_cnt[t] += add;
+        }
+        __syncthreads();
+    }
+    // publish and look back (thread t owns digit t)
+    {
+        uint32_t cnt = s_cnt[t];
+        volatile uint32_t *st = tile_status;
+        uint32_t excl = 0;
+        if (tile == 0) {
+            st[t] = RS_FLAG_INC | cnt;
+        } else {
+            st[(size_t)tile * RS_RADIX + t] = RS_FLAG_AGG | cnt;
+            int64_t j = (int64_t)tile - 1;
+            long spins = 0;
+            while (j >= 0) {
+                uint32_t v = st[(size_t)j * RS_RADIX + t];
+                uint32_t f = v & ~RS_MASK;
+                if (f == 0u) {
+                    if (++spins > RS_SPIN_LIMIT) {
+                        atomicOr(status, DEV_ERR_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                excl += v & RS_MASK;
+                if (f == RS_FLAG_INC) break;
+                --j;
+            }
+            st[(size_t)tile * RS_RADIX + t] = RS_FLAG_INC | (excl + cnt);
+        }
+        s_base[t] = offsets[t] + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t i = base + r * RS_THREADS + t;
+        if (i < n) {
+            uint32_t d = (key[r] >> shift) & 0xffu;
+            uint32_t pos = s_base[d] + rank[r];
+            if (pos < (uint32_t)n) {
+                kout[pos] = key[r];
+                vout[pos] = val[r];
+            }
+        }
+    }
+}
+
+// Sorts the pairs (keys, vals) of length *count (<= cap) by the low `bits`
+// key bits.  The inputs are only read; passes ping-pong between pair A and
+// pair B.  Returns 0 if the sorted pairs are in A, 1 if in B.
+int launch_radix_sort(Ctx &c, const uint32_t *keys, const uint32_t *vals, uint32_t *keys_a,
+                      uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const int *count,
+                      int64_t cap, int bits, uint32_t *scratch)
+{
+    int passes = (bits + 7) / 8;
+    if (passes < 1) passes = 1;
+    if (passes > 4) passes = 4;
+    size_t tiles = sort_tiles(cap);
+    uint32_t *ghist = scratch;
+    uint32_t *counters = scratch + 4 * RS_RADIX;
+    uint32_t *tstatus = counters + 4;
+    ESS_CUDA(cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * sort_scratch_words(cap), c.stream));
+    {
+        Launch L(c, "sort_hist");
+        unsigned blocks = (unsigned)(tiles < 1216 ? (tiles ? tiles : 1) : 1216);
+        k_rs_hist<<<blocks, RS_THREADS, 0, c.stream>>>(keys, count, passes, ghist);
+    }
+    {
+        Launch L(c, "sort_scan");
+        k_rs_scan<<<1, 1024, 0, c.stream>>>(ghist);
+    }
+    const uint32_t *ki = keys, *vi = vals;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t *ko = (p & 1) ? keys_b : keys_a, *vo = (p & 1) ? vals_b : vals_a;
+        {
+            Launch L(c, "sort_pass");
+            k_rs_pass<<<(unsigned)(tiles ? tiles : 1), RS_THREADS, 0, c.stream>>>(
+                ki, vi, ko, vo, count, 8 * p, ghist + p * RS_RADIX,
+                tstatus + (size_t)p * tiles * RS_RADIX, counters + p, c.dev_status);
+        }
+        ki = ko;
+        vi = vo;
+    }
+    return (passes & 1) ? 0 : 1;
+}
+
+// ----------------------------------------------------------- K6 Karras
+// Internal node i (0 <= i < n-1) of the binary radix tree over sorted unique
+// keys: direction from the longer common prefix with a neighbour, range end by
+// exponential then binary search, split by binary search on the common prefix
+// (Karras 2012).  Children: inner g as g, leaf g as -1-g.
+__device__ __forceinline__ int rs_delta(const uint32_t *k, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    return __clz(k[i] ^ k[j]);
+}
+
+__global__ void k_karras(const uint32_t *__restrict__ k, const int *__restrict__ count,
+                         int32_t *__restrict__ left, int32_t *__restrict__ right,
+                         int32_t *__restrict__ parent, int32_t *__restrict__ leaf_parent)
+{
+    int n = *count;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = rs_delta(k, n, i, i + 1) - rs_delta(k, n, i, i - 1) > 0 ? 1 : -1;
+    int dmin = rs_delta(k, n, i, i - d);
+    int lmax = 2;
+    while (rs_delta(k, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int l = 0;
+    for (int t = lmax / 2; t >= 1; t /= 2)
+        if (rs_delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = rs_delta(k, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) / 2;
+        if (rs_delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int g = i + s * d + (d < 0 ? d : 0);
+    int lo = min(i, j), hi = max(i, j);
+    int lc = (lo == g) ? -1 - g : g;
+    int rc = (hi == g + 1) ? -1 - (g + 1) : g + 1;
+    left[i] = lc;
+    right[i] = rc;
+    if (lc >= 0) parent[lc] = i; else leaf_parent[g] = i;
+    if (rc >= 0) parent[rc] = i; else leaf_parent[g + 1] = i;
+    if (i == 0) parent[0] = -1;
+}
+
+// ------------------------------------------------------- K7 bottom-up boxes
+// One thread per leaf climbs towards the root; at each inner node the first
+// arriving thread stops and the second (whose sibling subtree is complete)
+// unions the two child boxes, writes the node's box and its traversal node,
+// and climbs on.  Writers fence before the arrival counter; readers load with
+// .cg so that they see boxes written on other SMs.
+__device__ __forceinline__ void brick_box(uint32_t b, int gx, int gy, int32_t box[6])
+{
+    int x = (int)(b % (uint32_t)gx), y = (int)((b / (uint32_t)gx) % (uint32_t)gy);
+    int z = (int)(b / ((uint32_t)gx * (uint32_t)gy));
+    box[0] = x; box[1] = y; box[2] = z;
+    box[3] = x + 1; box[4] = y + 1; box[5] = z + 1;
+}
+
+__global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int *__restrict__ count,
+                              const int32_t *__restrict__ left, const int32_t *__restrict__ right,
+                              const int32_t *__restrict__ parent,
+                              const int32_t *__restrict__ leaf_parent, int *arrive,
+                              int32_t *inner_box, BoxNode *nodes, int32_t *root, int gx, int gy)
+{
+    int n = *count;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int32_t box[6];
+    brick_box(sorted_ids[j], gx, gy, box);
+    if (n == 1) {
+        // a single non-empty brick: the root is that leaf
+        root[0] = -1 - (int32_t)sorted_ids[0];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) root[1 + a] = box[a];
+        return;
+    }
+    int p = leaf_parent[j];
+    // a valid tree has at most 31 levels; the bound only guards a corrupt one
+    for (int level = 0; p >= 0 && p < n - 1 && level < 64; ++level) {
+        __threadfence();
+        if (atomicAdd(arrive + p, 1) == 0) return;
+        __threadfence();
+        int32_t lb[6], rb[6];
+        int lc = __ldcg(left + p), rc = __ldcg(right + p);
+        if (lc < 0) {
+            brick_box(__ldg(sorted_ids + (-1 - lc)), gx, gy, lb);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 6; ++a) lb[a] = __ldcg(inner_box + 6 * lc + a);
+        }
+        if (rc < 0) {
+            brick_box(__ldg(sorted_ids + (-1 - rc)), gx, gy, rb);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 6; ++a) rb[a] = __ldcg(inner_box + 6 * rc + a);
+        }
+        BoxNode nd;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            box[a] = min(lb[a], rb[a]);
+            box[3 + a] = max(lb[3 + a], rb[3 + a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+            inner_box[6 * p + a] = box[a];
+            nd.lbox[a] = (uint16_t)lb[a];
+            nd.rbox[a] = (uint16_t)rb[a];
+        }
+        nd.left = lc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - lc)) : lc;
+        nd.right = rc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - rc)) : rc;
+        nodes[p] = nd;
+        if (p == 0) {
+            root[0] = 0;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) root[1 + a] = box[a];
+        }
+        p = __ldcg(parent + p);
+    }
+}
+
+// Height of the tree (levels including root and leaves): each leaf counts its
+// ancestors.  Run on demand (structure info), not in the rebuild.
+__global__ void k_lbvh_height(const int *__restrict__ count, const int32_t *__restrict__ parent,
+                              const int32_t *__restrict__ leaf_parent, int *height)
+{
+    int n = *count;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int h = 1;
+    if (n >= 2) {
+        int p = leaf_parent[j];
+        while (p >= 0 && h <= 64) {
+            ++h;
+            p = parent[p];
+        }
+    }
+    atomicMax(height, h);
+}
+
+void launch_lbvh(Ctx &c, Structure &s)
+{
+    int64_t cap = s.nb;
+    int maxbits = 0;
+    for (int g : {s.gx, s.gy, s.gz}) {
+        int b = 0;
+        while ((1 << b) < g) ++b;
+        maxbits = b > maxbits ? b : maxbits;
+    }
+    int which = launch_radix_sort(c, s.keys, s.ids, s.keys_sorted, s.ids_sorted, s.keys_alt,
+                                  s.ids_alt, s.count, cap, 3 * maxbits, s.sort_scratch);
+    if (which == 1) {
+        // keep the invariant that keys_sorted / ids_sorted hold the result
+        std::swap(s.keys_sorted, s.keys_alt);
+        std::swap(s.ids_sorted, s.ids_alt);
+    }
+    unsigned blocks = (unsigned)((cap + 255) / 256);
+    ESS_CUDA(cudaMemsetAsync(s.arrive, 0, sizeof(int) * (size_t)(cap > 1 ? cap - 1 : 1), c.stream));
+    {
+        Launch L(c, "lbvh_karras");
+        k_karras<<<blocks, 256, 0, c.stream>>>(s.keys_sorted, s.count, s.left, s.right, s.parent,
+                                               s.leaf_parent);
+    }
+    {
+        Launch L(c, "lbvh_bounds");
+        k_lbvh_bounds<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
+                                                    s.parent, s.leaf_parent, s.arrive,
+                                                    s.inner_box, s.nodes, s.root, s.gx, s.gy);
+    }
+}
+
+int lbvh_height(Ctx &c, Structure &s)
+{
+    int *d = (int *)c.alloc(sizeof(int));
+    ESS_CUDA(cudaMemsetAsync(d, 0, sizeof(int), c.stream));
+    {
+        Launch L(c, "lbvh_height");
+        k_lbvh_height<<<(unsigned)((s.nb + 255) / 256), 256, 0, c.stream>>>(s.count, s.parent,
+                                                                            s.leaf_parent, d);
+    }
+    int h = 0;
+    ESS_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    ESS_CUDA(cudaStreamSynchronize(c.stream));
+    c.free(d);
+    return h;
+}
+
+}  // namespace ess

@@ -35,6 +35,11 @@ struct RArgs {
     // macrocell grid / brick raster
     const uint8_t *mask;
     int B, gx, gy, gz;
+    // box trees (LBVH, k-d)
+    const BoxNode *nodes;
+    const int32_t *root;      // ref, box lo xyz, hi xyz (brick coordinates)
+    const int *count;         // > 0 iff the tree is non-empty
+    const int16_t *leaf_box;  // k-d: leaf boxes (6 per leaf)
     unsigned long long *samples;
 };
 
@@ -238,6 +243,107 @@ __device__ __forceinline__ void trace_grid(const RArgs &a, const Ray &r, float t
     }
 }
 
+// Box in brick coordinates [lo, hi) -> closed voxel-space box, clamped at the
+// volume's far faces (partial bricks).
+__device__ __forceinline__ void brick_box_f(const RArgs &a, int lx, int ly, int lz, int hx, int hy,
+                                            int hz, float lo[3], float hi[3])
+{
+    lo[0] = (float)(lx * a.B);
+    lo[1] = (float)(ly * a.B);
+    lo[2] = (float)(lz * a.B);
+    hi[0] = (float)min(hx * a.B, a.nx);
+    hi[1] = (float)min(hy * a.B, a.ny);
+    hi[2] = (float)min(hz * a.B, a.nz);
+}
+
+__device__ __forceinline__ void leaf_box_f(const RArgs &a, int KIND, int32_t ref, float lo[3],
+                                           float hi[3])
+{
+    int32_t id = -1 - ref;
+    if (KIND == ESS_LBVH) {
+        int x = id % a.gx, y = (id / a.gx) % a.gy, z = id / (a.gx * a.gy);
+        brick_box_f(a, x, y, z, x + 1, y + 1, z + 1, lo, hi);
+    } else {
+        const int16_t *b = a.leaf_box + 6 * (size_t)id;
+        brick_box_f(a, __ldg(b), __ldg(b + 1), __ldg(b + 2), __ldg(b + 3), __ldg(b + 4),
+                    __ldg(b + 5), lo, hi);
+    }
+}
+
+// Ordered traversal of a binary box tree.  Each inner node carries both
+// children's boxes; both are slab-tested, the child entered first is
+// visited first and the other is pushed (LBVH children are separated by the
+// Morton split plane and k-d children by the split plane, so entry order is
+// front-to-back order).  A leaf's box interval is marched with rule S.  The
+// stack of STACK entries suffices because the build guarantees a height of at
+// most STACK + 1 levels (30-bit Morton keys give LBVH heights <= 31).
+template <typename T, int KIND, int STACK>
+__device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float tn, float tf,
+                                           Acc &acc, long long &ns)
+{
+    const int n = __ldg(a.count);
+    if (n <= 0) return;
+    // reference bounds: a valid tree never leaves them and visits each node at
+    // most once per ray; the checks keep a corrupt structure from reading
+    // outside its buffers or looping
+    const int n_inner = KIND == ESS_LBVH ? n - 1 : n;
+    const int64_t n_leaf = KIND == ESS_LBVH ? (int64_t)a.gx * a.gy * a.gz : n;
+    int budget = 2 * n + 1;
+    int32_t ref = __ldg(a.root);
+    {
+        float lo[3], hi[3];
+        brick_box_f(a, __ldg(a.root + 1), __ldg(a.root + 2), __ldg(a.root + 3), __ldg(a.root + 4),
+                    __ldg(a.root + 5), __ldg(a.root + 6), lo, hi);
+        float ta = tn, tb = tf;
+        slab(r, lo, hi, ta, tb);
+        if (!(ta <= tb)) return;
+    }
+    int32_t stack[STACK];
+    int sp = 0;
+    int k_next = 0;
+    while (--budget >= 0) {
+        if (ref < 0) {
+            if (-1 - (int64_t)ref >= n_leaf) return;
+            float lo[3], hi[3];
+            leaf_box_f(a, KIND, ref, lo, hi);
+            float ta = tn, tb = tf;
+            slab(r, lo, hi, ta, tb);
+            if (ta <= tb && march<T>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
+        } else {
+            if (ref >= n_inner) return;
+            const uint4 *q = reinterpret_cast<const uint4 *>(a.nodes + ref);
+            uint4 q0 = __ldg(q), q1 = __ldg(q + 1);
+            // lbox = q0.x..q0.z (6 x u16), rbox = q0.w, q1.x, q1.y; left = q1.z, right = q1.w
+            float llo[3], lhi[3], rlo[3], rhi[3];
+            brick_box_f(a, q0.x & 0xffff, q0.x >> 16, q0.y & 0xffff, q0.y >> 16, q0.z & 0xffff,
+                        q0.z >> 16, llo, lhi);
+            brick_box_f(a, q0.w & 0xffff, q0.w >> 16, q1.x & 0xffff, q1.x >> 16, q1.y & 0xffff,
+                        q1.y >> 16, rlo, rhi);
+            float la = tn, lb = tf, ra = tn, rb = tf;
+            slab(r, llo, lhi, la, lb);
+            slab(r, rlo, rhi, ra, rb);
+            bool hl = la <= lb, hr = ra <= rb;
+            int32_t lc = (int32_t)q1.z, rc = (int32_t)q1.w;
+            if (hl && hr) {
+                bool left_first = la <= ra;
+                if (sp < STACK) stack[sp++] = left_first ? rc : lc;
+                ref = left_first ? lc : rc;
+                continue;
+            }
+            if (hl) {
+                ref = lc;
+                continue;
+            }
+            if (hr) {
+                ref = rc;
+                continue;
+            }
+        }
+        if (sp == 0) return;
+        ref = stack[--sp];
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 // 128 threads per block, 16 x 8 pixels; each warp covers an 8 x 4 tile so
 // that its rays stay close together.
@@ -261,6 +367,10 @@ __global__ void __launch_bounds__(128) k_render(RArgs a)
                 trace_naive<T>(a, r, tn, tf, acc, ns);
             else if (KIND == ESS_GRID)
                 trace_grid<T>(a, r, tn, tf, acc, ns);
+            else if (KIND == ESS_LBVH)
+                trace_tree<T, ESS_LBVH, 32>(a, r, tn, tf, acc, ns);
+            else
+                trace_tree<T, ESS_KD, 128>(a, r, tn, tf, acc, ns);
         }
         float one_m = 1.0f - acc.a;
         a.out[(size_t)y * a.W + x] =
@@ -311,6 +421,10 @@ void launch_render(Ctx &c, const RenderJob &j)
     a.gx = j.st->gx;
     a.gy = j.st->gy;
     a.gz = j.st->gz;
+    a.nodes = j.st->nodes;
+    a.root = j.st->root;
+    a.count = j.st->kind == ESS_KD ? j.st->kd_count_dev : j.st->count;
+    a.leaf_box = j.st->kd_leaf_box;
     a.samples = c.samples;
     switch (j.st->kind) {
     case ESS_NONE: {
@@ -321,6 +435,16 @@ void launch_render(Ctx &c, const RenderJob &j)
     case ESS_GRID: {
         Launch L(c, "render_grid");
         launch_kind<ESS_GRID>(c, a, j.vol->dtype);
+        break;
+    }
+    case ESS_LBVH: {
+        Launch L(c, "render_lbvh");
+        launch_kind<ESS_LBVH>(c, a, j.vol->dtype);
+        break;
+    }
+    case ESS_KD: {
+        Launch L(c, "render_kd");
+        launch_kind<ESS_KD>(c, a, j.vol->dtype);
         break;
     }
     default: throw Error{ESS_ERR_ARG, "render: structure kind not supported"};

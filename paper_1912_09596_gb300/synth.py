@@ -236,7 +236,7 @@ def tf_window(nt, lo, hi, alpha_max=0.6) -> np.ndarray:
 # alpha windows (entry ranges of a 256-entry table) used with ct_like_u8; they
 # select different shells / vessels and give 5-30 % non-empty 8^3 bricks.
 CT_WINDOWS = [(200, 255), (150, 185), (100, 135), (60, 90), (190, 230),
-              (110, 180), (220, 255), (55, 125)]
+              (110, 180), (216, 255), (55, 125)]
 
 
 def tf_set_ct(nt=256):
