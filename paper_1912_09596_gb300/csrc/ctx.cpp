@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -202,8 +203,14 @@ void free_structure(Ctx &c, Structure &s)
     void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_sorted, s.ids_sorted,
                     s.keys_alt, s.ids_alt, s.sort_scratch, s.left, s.right, s.parent,
                     s.leaf_parent, s.inner_box, s.arrive, s.nodes, s.root, s.kd_nodes,
-                    s.kd_leaf_box, s.kd_count_dev, s.kd_aux, s.brick_node};
+                    s.kd_count_dev, s.brick_node, s.kd_scratch_i32, s.kd_splits_dev};
     for (void *p : ptrs) c.free(p);
+    kd_free(c, s);
+    if (s.kd_splits_host) {
+        cudaStreamSynchronize(c.stream);
+        cudaFreeHost(s.kd_splits_host);
+        s.kd_splits_host = nullptr;
+    }
 }
 
 template <typename P> P *alloc_n(Ctx &c, Structure &s, size_t n)
@@ -233,6 +240,31 @@ void alloc_lbvh(Ctx &c, Structure &s)
     s.root = alloc_n<int32_t>(c, s, 8);
 }
 
+// Device buffers of a k-d tree over up to nb bricks (Sec. 3.2): a full binary
+// tree whose leaves hold at least one brick has at most 2 nb - 1 nodes.
+void alloc_kd(Ctx &c, Structure &s)
+{
+    size_t cap = (size_t)s.nb;
+    s.kd_capacity = (int)std::min<size_t>(2 * cap, (size_t)INT32_MAX / 16);
+    s.kd_nodes = alloc_n<int32_t>(c, s, 9 * (size_t)s.kd_capacity);
+    s.nodes = alloc_n<BoxNode>(c, s, (size_t)s.kd_capacity);
+    s.root = alloc_n<int32_t>(c, s, 8);
+    s.kd_count_dev = alloc_n<int>(c, s, 1);
+    s.brick_node = alloc_n<int>(c, s, cap);
+    s.kd_scratch_i32 = alloc_n<int32_t>(c, s, 8);
+    s.kd_splits_dev = alloc_n<int>(c, s, 1);
+    ESS_CUDA(cudaMallocHost(&s.kd_splits_host, sizeof(int)));
+}
+
+int64_t nonempty_count_sync(Ctx &c, Structure &s)
+{
+    int n = 0;
+    ESS_CUDA(cudaMemcpyAsync(&n, s.count, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    ESS_CUDA(cudaStreamSynchronize(c.stream));
+    s.n_host = n;
+    return n;
+}
+
 // The empty test and compaction (Sec. 3.1), then the kind-specific build.
 void run_build(Ctx &c, Structure &s)
 {
@@ -248,9 +280,13 @@ void run_build(Ctx &c, Structure &s)
     }
     launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums,
                    s.kind == ESS_LBVH ? s.keys : nullptr, s.gx, s.gy);
-    if (s.kind == ESS_LBVH) launch_lbvh(c, s);
     s.n_host = -1;
     s.height = -1;
+    if (s.kind == ESS_LBVH) launch_lbvh(c, s);
+    if (s.kind == ESS_KD) {
+        s.volume = &v;
+        launch_kd(c, s, nonempty_count_sync(c, s));
+    }
     s.tf_version = t.version;
 }
 
@@ -464,8 +500,8 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         ESS_REQUIRE(structure, "null pointer");
         Volume &v = get_vol(c, vol);
         TF &t = get_tf(c, tf);
-        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_NONE,
-                    "structure kind not available in this build");
+        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_KD || kind == ESS_NONE,
+                    "unknown structure kind");
         ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0};
         auto s = std::make_unique<Structure>();
         s->kind = kind;
@@ -473,7 +509,8 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         s->tf = tf;
         if (kind != ESS_NONE) {
             ESS_REQUIRE(p.brick >= 2 && p.brick <= 64, "brick must be in 2..64");
-            ESS_REQUIRE(p.nbins == 0 || (p.nbins >= 2 && p.nbins <= 64), "nbins must be 0 or 2..64");
+            ESS_REQUIRE(p.nbins == 0 || (p.nbins >= 2 && p.nbins <= 64 && p.nbins % 2 == 0),
+                        "nbins must be 0 or even in 2..64");
             ESS_REQUIRE(p.halting == 0 || p.halting == 1, "halting must be 0 or 1");
             ESS_REQUIRE(p.mls >= 0, "mls must be >= 0");
             ESS_REQUIRE(p.empty_test == 0 || p.empty_test == 1, "empty_test must be 0 or 1");
@@ -494,12 +531,13 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
             if (kind == ESS_LBVH) {
                 ESS_REQUIRE(s->gx <= 1024 && s->gy <= 1024 && s->gz <= 1024,
                             "LBVH: at most 1024 bricks per axis (30-bit Morton codes)");
-                try {
-                    alloc_lbvh(c, *s);
-                } catch (...) {
-                    free_structure(c, *s);
-                    throw;
-                }
+            }
+            try {
+                if (kind == ESS_LBVH) alloc_lbvh(c, *s);
+                if (kind == ESS_KD) alloc_kd(c, *s);
+            } catch (...) {
+                free_structure(c, *s);
+                throw;
             }
         }
         s->p = p;
@@ -551,6 +589,10 @@ ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_struct
             if (s.height < 0) s.height = n > 0 ? lbvh_height(c, s) : 0;
             info->height = s.height;
         }
+        if (s.kind == ESS_KD) {
+            info->n_nodes = s.kd_count;
+            info->height = s.height;
+        }
         info->device_bytes = s.device_bytes;
     });
 }
@@ -592,6 +634,10 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
             copy_out(c, dst, src, bytes, capacity, written);
             break;
         }
+        case ESS_ARR_KD_NODES:
+            ESS_REQUIRE(s.kind == ESS_KD, "array only exists for a k-d tree");
+            copy_out(c, dst, s.kd_nodes, sizeof(int32_t) * 9 * (size_t)s.kd_count, capacity, written);
+            break;
         default: throw Error{ESS_ERR_ARG, "array not available for this structure kind"};
         }
     });

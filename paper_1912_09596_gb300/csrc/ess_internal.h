@@ -106,17 +106,30 @@ struct Structure {
     int32_t *root = nullptr;       // device root record: ref, box lo xyz, hi xyz, pad
     int height = 0;
     // k-d
-    int32_t *kd_nodes = nullptr;   // max_nodes x 9 (debug / parity layout)
+    Volume *volume = nullptr;
+    int32_t *kd_nodes = nullptr;     // capacity x 9: lo xyz, hi xyz, axis, plane, first child
     int kd_capacity = 0;
     int64_t kd_count = 0;
-    int16_t *kd_leaf_box = nullptr;  // leaves x 6 (brick coordinates)
+    int kd_count_i32 = 0;
     int *kd_count_dev = nullptr;     // device: k-d node count
-    int32_t *kd_aux = nullptr;       // scratch for the level loop
-    size_t kd_aux_bytes = 0;
-    int *brick_node = nullptr;       // per non-empty brick: current node
+    int *brick_node = nullptr;       // per non-empty brick: its node on the current level
+    int32_t *kd_scratch_i32 = nullptr;  // root box reduction
+    int32_t *kd_slabs[2] = {nullptr, nullptr};  // per-level slab boxes (ping-pong)
+    size_t kd_slab_cap[2] = {0, 0};             // in nodes
+    unsigned long long *kd_vr = nullptr;        // suffix volumes
+    size_t kd_vr_cap = 0;
+    void *kd_dec = nullptr;                     // per-node decisions
+    size_t kd_dec_cap = 0;
+    uint32_t *kd_block_sums = nullptr;
+    size_t kd_bs_cap = 0;
+    int *kd_splits_dev = nullptr;
+    int *kd_splits_host = nullptr;              // pinned
     size_t device_bytes = 0;
     bool released = false;
 };
+
+// The k-d renderer keeps a stack of 128 entries, enough for 129 levels.
+constexpr int KD_MAX_LEVELS = 129;
 
 // ---------------------------------------------------------------- context
 struct Ctx {
@@ -178,6 +191,11 @@ int launch_radix_sort(Ctx &c, const uint32_t *keys, const uint32_t *vals, uint32
                       int64_t cap, int bits, uint32_t *scratch);
 void launch_lbvh(Ctx &c, Structure &s);
 int lbvh_height(Ctx &c, Structure &s);
+
+// kd.cu
+void launch_kd(Ctx &c, Structure &s, int64_t n);
+void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur);
+void kd_free(Ctx &c, Structure &s);
 
 // render.cu
 struct RenderJob {

@@ -228,12 +228,14 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
                 int32_t acc[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
                 for (int j = ns - 1; j >= 1; --j) {
                     box_union(acc, sl + 6 * j);
-                    v[j] = kd_volume(acc, P);
+                    v[j] = acc[0] == INT_MAX ? ~0ull : kd_volume(acc, P);
                 }
                 int32_t pre[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
                 for (int j = 1; j < ns; ++j) {
                     box_union(pre, sl + 6 * (j - 1));
-                    if (pre[0] == INT_MAX || v[j] == 0) continue;
+                    // both sides are non-empty for a tight node box; the test
+                    // only guards the definition
+                    if (pre[0] == INT_MAX || v[j] == ~0ull) continue;
                     unsigned long long cost = kd_volume(pre, P) + v[j];
                     if (cost < best) {
                         best = cost;
@@ -402,6 +404,44 @@ __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const int *__restr
 }
 
 // ------------------------------------------------------------------ host
+// Per-level buffers: the current level's slabs were reset by the previous
+// level's emit and already fit; the next level (at most twice as many nodes)
+// may need a larger buffer, whose old contents are not needed.
+void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur)
+{
+    size_t slab_words = (size_t)3 * S * 6;
+    auto grow = [&](void *&p, size_t &cap, size_t need, size_t elem) {
+        if (cap >= need) return;
+        c.free(p);
+        size_t n = std::max(need, cap * 2);
+        p = c.alloc(n * elem);
+        cap = n;
+    };
+    if (s.kd_slab_cap[cur] < (size_t)lvl_size)
+        throw Error{ESS_ERR_ARG, "internal: k-d slab buffer of the current level too small"};
+    void *nx = s.kd_slabs[cur ^ 1];
+    grow(nx, s.kd_slab_cap[cur ^ 1], (size_t)2 * lvl_size, slab_words * sizeof(int32_t));
+    s.kd_slabs[cur ^ 1] = (int32_t *)nx;
+    void *vr = s.kd_vr;
+    grow(vr, s.kd_vr_cap, (size_t)lvl_size * 3 * S, sizeof(unsigned long long));
+    s.kd_vr = (unsigned long long *)vr;
+    grow(s.kd_dec, s.kd_dec_cap, (size_t)lvl_size, sizeof(KdDecision));
+    void *bs = s.kd_block_sums;
+    grow(bs, s.kd_bs_cap, (size_t)(lvl_size + 255) / 256, sizeof(uint32_t));
+    s.kd_block_sums = (uint32_t *)bs;
+}
+
+void kd_free(Ctx &c, Structure &s)
+{
+    void *ptrs[] = {s.kd_slabs[0], s.kd_slabs[1], s.kd_vr, s.kd_dec, s.kd_block_sums};
+    for (void *p : ptrs) c.free(p);
+    s.kd_slabs[0] = s.kd_slabs[1] = nullptr;
+    s.kd_vr = nullptr;
+    s.kd_dec = nullptr;
+    s.kd_block_sums = nullptr;
+    s.kd_slab_cap[0] = s.kd_slab_cap[1] = s.kd_vr_cap = s.kd_dec_cap = s.kd_bs_cap = 0;
+}
+
 static int kd_slots(const Structure &s)
 {
     if (s.p.nbins != 0) return s.p.nbins;
@@ -439,7 +479,11 @@ void launch_kd(Ctx &c, Structure &s, int64_t n)
         k_kd_root_reduce<<<bricks_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.gx, s.gy,
                                                               root_box);
     }
-    c.kd_reserve(s, 1, P.S);
+    if (s.kd_slab_cap[0] < 1) {
+        c.free(s.kd_slabs[0]);
+        s.kd_slabs[0] = (int32_t *)c.alloc(sizeof(int32_t) * 3 * P.S * 6 * 16);
+        s.kd_slab_cap[0] = 16;
+    }
     {
         Launch L(c, "kd_init");
         k_kd_init<<<1, 256, 0, c.stream>>>(root_box, s.kd_nodes, s.kd_slabs[0], P.S);
@@ -451,7 +495,7 @@ void launch_kd(Ctx &c, Structure &s, int64_t n)
         if (levels > KD_MAX_LEVELS)
             throw Error{ESS_ERR_ARG, "k-d tree deeper than " + std::to_string(KD_MAX_LEVELS) +
                                          " levels (renderer stack limit)"};
-        c.kd_reserve(s, lvl_size, P.S);  // slabs for this level and 2x for the next
+        kd_reserve(c, s, lvl_size, P.S, cur);  // slabs for this level and 2x for the next
         unsigned nblk = (unsigned)((lvl_size + 255) / 256);
         {
             Launch L(c, "kd_accumulate");
@@ -490,8 +534,6 @@ void launch_kd(Ctx &c, Structure &s, int64_t n)
     }
     s.kd_count = lvl_begin;
     s.height = levels;
-    ESS_CUDA(cudaMemcpyAsync(s.kd_count_dev, &s.kd_count_i32, sizeof(int), cudaMemcpyHostToDevice,
-                             c.stream));
     s.kd_count_i32 = (int)s.kd_count;
     ESS_CUDA(cudaMemcpyAsync(s.kd_count_dev, &s.kd_count_i32, sizeof(int), cudaMemcpyHostToDevice,
                              c.stream));

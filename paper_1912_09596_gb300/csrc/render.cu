@@ -39,7 +39,7 @@ struct RArgs {
     const BoxNode *nodes;
     const int32_t *root;      // ref, box lo xyz, hi xyz (brick coordinates)
     const int *count;         // > 0 iff the tree is non-empty
-    const int16_t *leaf_box;  // k-d: leaf boxes (6 per leaf)
+    const int32_t *kd_nodes;  // k-d: node records, 9 ints (box first)
     unsigned long long *samples;
 };
 
@@ -264,7 +264,7 @@ __device__ __forceinline__ void leaf_box_f(const RArgs &a, int KIND, int32_t ref
         int x = id % a.gx, y = (id / a.gx) % a.gy, z = id / (a.gx * a.gy);
         brick_box_f(a, x, y, z, x + 1, y + 1, z + 1, lo, hi);
     } else {
-        const int16_t *b = a.leaf_box + 6 * (size_t)id;
+        const int32_t *b = a.kd_nodes + 9 * (size_t)id;
         brick_box_f(a, __ldg(b), __ldg(b + 1), __ldg(b + 2), __ldg(b + 3), __ldg(b + 4),
                     __ldg(b + 5), lo, hi);
     }
@@ -424,7 +424,7 @@ void launch_render(Ctx &c, const RenderJob &j)
     a.nodes = j.st->nodes;
     a.root = j.st->root;
     a.count = j.st->kind == ESS_KD ? j.st->kd_count_dev : j.st->count;
-    a.leaf_box = j.st->kd_leaf_box;
+    a.kd_nodes = j.st->kd_nodes;
     a.samples = c.samples;
     switch (j.st->kind) {
     case ESS_NONE: {

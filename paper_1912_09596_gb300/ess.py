@@ -24,7 +24,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_HANDLE, ERR_TIMEOUT, ERR_BUSY, ERR_STALE = 0
 U8, U16, F32 = 0, 1, 2
 GRID, LBVH, KD, NONE = 0, 1, 2, 3
 KIND_NAMES = {GRID: "grid", LBVH: "lbvh", KD: "kd", NONE: "none"}
-KINDS = (NONE, GRID, LBVH)   # structure kinds this library builds
+KINDS = (NONE, GRID, LBVH, KD)   # structure kinds this library builds
 (ARR_MINMAX, ARR_MASK, ARR_IDS, ARR_KEYS, ARR_SORTED_KEYS, ARR_SORTED_IDS, ARR_LBVH_LEFT,
  ARR_LBVH_RIGHT, ARR_LBVH_BOXES, ARR_KD_NODES) = range(10)
 
