@@ -208,6 +208,28 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
                       const ess_render_params *params, int W, int H, float *out,
                       int out_on_device);
 
+/* ------------------------------------------------------ allocation-free */
+
+/* Brick compaction without any allocation: writes to `ids` the indices of the
+ * non-zero bytes of the device byte mask `mask` (n_bricks bytes), in
+ * increasing order, and their number to the device int `*count`; the same
+ * result as the ids (ESS_ARR_IDS) that ess_build keeps for the mask it
+ * computes.  The paper has no counterpart: this is for callers that cannot
+ * allocate device memory (their memory is pre-reserved by another allocator,
+ * or a cudaMalloc would stall their frame loop).  All pointers are device
+ * memory owned by the caller; `ids` must hold n_bricks uint32 values.  Work is
+ * queued on `cuda_stream` (NULL: the default stream) and the call returns
+ * without waiting.  The only scratch is a 16 KiB file-scope device array,
+ * allocated when the library is loaded and kept on every GPU that loads it;
+ * the first call on a device looks up its address, so make that first call
+ * before any stream capture.  All calls share that array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.
+ * Errors: ESS_ERR_ARG for n_bricks < 0 or above 16,777,216 (4096 tiles of
+ * 4096 flags) or a null pointer; ESS_ERR_CUDA if a launch fails.  No
+ * ess_last_error message (there is no context). */
+ess_status ess_compact_mask_noalloc(const uint8_t *mask, int64_t n_bricks, uint32_t *ids,
+                                    int *count, void *cuda_stream);
+
 /* -------------------------------------------------------------- profiling */
 
 /* Number of ray samples evaluated (classified and composited) by all renders

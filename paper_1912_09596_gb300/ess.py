@@ -82,6 +82,7 @@ def _load():
         "ess_profile_enable": [vp, i],
         "ess_profile_read": [vp, i, P(C.c_char_p), P(C.c_uint64), P(C.c_double), P(i)],
         "ess_profile_reset": [vp],
+        "ess_compact_mask_noalloc": [vp, C.c_int64, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -240,6 +241,17 @@ def ess_render(ctx, structure, cam, params, W, H, out):
     p, dev = _ptr(out)
     _check(ctx, lib.ess_render(ctx, structure, C.byref(cam), C.byref(params), W, H, p, dev))
     return out
+
+
+def ess_compact_mask_noalloc(mask, ids, count, stream=None):
+    """`mask`: device uint8 tensor of n bricks; `ids`: device int32/uint32
+    tensor of at least n entries; `count`: device int32 tensor of 1 entry.
+    Raises EssError on a non-OK status (there is no context message)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    st = lib.ess_compact_mask_noalloc(_ptr(mask)[0], int(mask.numel()), _ptr(ids)[0],
+                                      _ptr(count)[0], C.c_void_p(raw) if raw else None)
+    if st != OK:
+        raise EssError(st, "ess_compact_mask_noalloc failed")
 
 
 def ess_launch_count(ctx):
