@@ -98,6 +98,14 @@ ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
                              ess_dtype dtype, int nx, int ny, int nz,
                              float value_lo, float value_hi, ess_handle *vol);
 
+/* Chooses how renders read voxels (the image is the same either way):
+ * cells = 1 keeps a corner-replicated copy of the volume, (nx+1)(ny+1)(nz+1)
+ * cells of the 8 clamped voxels one trilinear sample interpolates (8x the
+ * volume's bytes; one vector load per sample); cells = 0 drops that copy and
+ * reads the 8 voxels from the volume itself.  ess_volume_upload keeps the copy
+ * when it fits in half of the free device memory. */
+ess_status ess_volume_set_sampler(ess_ctx *ctx, ess_handle vol, int cells);
+
 /* Sets an RGBA transfer function of `nt` entries (Sec. 1: the colour and
  * alpha TF that maps scalar values to colour and opacity), `rgba` = nt*4
  * floats, entry-major.  Alpha must lie in [0, 1] and every value must be
@@ -196,6 +204,9 @@ typedef struct {
     float ert;    /* early ray termination: stop once opacity >= ert; a value
                      above 1 disables it (the paper's benchmarks, Sec. 4.1) */
     float bg[4];  /* background RGBA composited behind the volume */
+    int tile_w;   /* warp tile width in pixels: 4, 8, 16 or 32 (0 = 8); the
+                     warp covers tile_w x (32 / tile_w) pixels.  Does not
+                     change the image. */
 } ess_render_params;
 
 /* Ray-marches `structure` (Sec. 4.1: absorption plus emission,
@@ -207,6 +218,105 @@ typedef struct {
 ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *camera,
                       const ess_render_params *params, int W, int H, float *out,
                       int out_on_device);
+
+/* ----------------------------------------------------------------- batched */
+
+typedef struct {
+    ess_handle structure;      /* built structure (its volume and TF) */
+    ess_camera camera;
+    ess_render_params params;  /* tile_w is taken from the batch call */
+    int W, H;
+    float *out;                /* device memory, W*H*4 floats, caller-owned */
+} ess_render_item;
+
+/* Renders `count` images in one persistent launch per (volume dtype,
+ * structure kind) group: blocks take 128-pixel tiles of all images from one
+ * work counter, so many TFs, views and uneven image sizes share the GPU.  The
+ * launch is captured once as a CUDA graph and replayed.  Every image equals
+ * what ess_render gives for the same item, bit for bit.  Asynchronous on the
+ * context stream; 1 <= count <= 4096.  ESS_ERR_STALE if any structure's TF
+ * was updated after its build. */
+ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int count, int tile_w);
+
+/* ------------------------------------------------------------------ tuning */
+
+typedef struct {
+    int kind;      /* ESS_GRID, ESS_LBVH or ESS_KD */
+    int brick;     /* brick edge */
+    int tile_w;    /* warp tile width for ess_render_params.tile_w */
+    float build_ms, render_ms;  /* measured: one rebuild, mean of one frame per camera */
+} ess_tune_result;
+
+/* Autotuner: builds every candidate structure kind x brick size (4, 8, 16, 32;
+ * k-d deep, 4 bins, maximum leaf 32^3) for `vol` and `tf`, renders the
+ * `ncam` cameras with every warp tile width, and returns the candidate with
+ * the least build_ms + frames_per_edit * render_ms (CUDA-event times).
+ * Synchronous; the candidate structures are released again. */
+ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_camera *cameras,
+                        int ncam, const ess_render_params *params, int W, int H,
+                        float frames_per_edit, ess_tune_result *best);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct ess_server ess_server;  /* opaque */
+
+typedef struct {
+    size_t memory_budget;  /* device bytes for the outputs of admitted requests
+                              (0: a quarter of the free memory at creation) */
+    int max_batch;         /* renders per batched launch, 1..4096 */
+    int max_inflight;      /* batches on the GPU at once, 1..64 */
+    int tile_w;            /* warp tile width of the batched launches (0 = 8) */
+} ess_server_config;
+
+typedef enum {
+    ESS_REQ_RENDER = 0,  /* render a view of a structure */
+    ESS_REQ_EDIT = 1     /* replace the structure's TF, rebuild it, then render */
+} ess_request_kind;
+
+typedef struct {
+    int kind;                  /* ess_request_kind */
+    ess_handle structure;
+    const float *rgba;         /* ESS_REQ_EDIT: new table, host memory, nt x 4,
+                                  copied by ess_server_submit */
+    int nt;
+    ess_camera camera;
+    ess_render_params params;
+    int W, H;
+    float *out;                /* host memory for the W*H*4 float image; it must
+                                  stay valid until the request is done */
+} ess_request;
+
+typedef struct {
+    int done;            /* 1 once the image is in `out` */
+    ess_status status;   /* result of the request */
+    double queue_ms;     /* submission to launch */
+    double latency_ms;   /* submission to the image in host memory */
+} ess_request_status;
+
+/* Starts a request loop on `ctx` (the paper's interactive use, Sec. 1: views
+ * and TF edits of resident volumes).  A worker thread admits queued requests
+ * in arrival order into batches while their output memory fits the budget,
+ * applies the batch's edits (TF upload + rebuild), renders the batch in one
+ * persistent launch and copies each image to its host buffer; up to
+ * max_inflight batches run on the GPU while the next one is admitted.  Each
+ * image equals what ess_render gives for the request alone.  While the server
+ * runs, the context must not be used directly; destroy the server before the
+ * context.  A request larger than the whole budget ends with ESS_ERR_BUSY. */
+ess_status ess_server_create(ess_ctx *ctx, const ess_server_config *cfg, ess_server **out);
+
+/* Queues a request (thread-safe); `*id` identifies it.  ESS_ERR_ARG for a bad
+ * request, ESS_ERR_BUSY after the server began to stop. */
+ess_status ess_server_submit(ess_server *s, const ess_request *req, uint64_t *id);
+
+/* Reports a request's state without waiting / after waiting for it. */
+ess_status ess_server_poll(ess_server *s, uint64_t id, ess_request_status *st);
+ess_status ess_server_wait(ess_server *s, uint64_t id, ess_request_status *st);
+
+/* Waits until every submitted request is done. */
+ess_status ess_server_drain(ess_server *s);
+
+/* Finishes all submitted requests, stops the worker and frees the server. */
+ess_status ess_server_destroy(ess_server *s);
 
 /* ------------------------------------------------------ allocation-free */
 

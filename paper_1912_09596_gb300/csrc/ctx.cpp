@@ -13,10 +13,6 @@
 
 #include "ess_internal.h"
 
-struct ess_ctx {
-    ess::Ctx c;
-};
-
 namespace ess {
 
 // ------------------------------------------------------------ memory, events
@@ -183,8 +179,29 @@ void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
         if (!t.staged) ESS_CUDA(cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
         ESS_CUDA(cudaEventRecord(t.staged, c.stream));
     }
+    // entry nt repeats entry nt-1 so that the renderer's upper neighbour needs no clamp
+    ESS_CUDA(cudaMemcpyAsync(t.table + t.nt, t.table + (t.nt - 1), sizeof(float4),
+                             cudaMemcpyDeviceToDevice, c.stream));
     launch_tf_prefix(c, t.table, t.nt, t.prefix, on_device);
     ++t.version;
+}
+
+// Builds (mode 1) or drops (mode 0) the corner-replicated cell copy.
+void set_sampler(Ctx &c, Volume &v, int mode)
+{
+    if (mode == 1) {
+        if (!v.cells) {
+            v.cell_bytes = cell_array_bytes(v);
+            v.cells = c.alloc(v.cell_bytes);
+            launch_build_cells(c, v, v.cells);
+        }
+        v.use_cells = true;
+    } else {
+        c.free(v.cells);
+        v.cells = nullptr;
+        v.cell_bytes = 0;
+        v.use_cells = false;
+    }
 }
 
 float2 *minmax_for(Ctx &c, Volume &v, int B)
@@ -301,6 +318,22 @@ int64_t nonempty_count(Ctx &c, Structure &s)
     return s.n_host;
 }
 
+void check_render_args(const ess_camera *camera, const ess_render_params *params, int W, int H)
+{
+    ESS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "image size must be in 1..16384");
+    ESS_REQUIRE(params->dt >= 1e-3f && params->dt <= 1e4f, "dt must be in [1e-3, 1e4]");
+    ESS_REQUIRE(std::isfinite(params->ert), "ert must be finite");
+    ESS_REQUIRE(params->tile_w == 0 || params->tile_w == 4 || params->tile_w == 8 ||
+                    params->tile_w == 16 || params->tile_w == 32,
+                "tile_w must be 0, 4, 8, 16 or 32");
+    for (int i = 0; i < 3; ++i)
+        ESS_REQUIRE(std::isfinite(camera->eye[i]) && std::isfinite(camera->u[i]) &&
+                        std::isfinite(camera->v[i]) && std::isfinite(camera->w[i]),
+                    "camera must be finite");
+    ESS_REQUIRE(camera->w[0] != 0.0f || camera->w[1] != 0.0f || camera->w[2] != 0.0f,
+                "camera needs a non-zero forward vector");
+}
+
 void copy_out(Ctx &c, void *dst, const void *src, size_t bytes, size_t cap, size_t *written)
 {
     if (bytes > cap) throw Error{ESS_ERR_ARG, "destination buffer too small"};
@@ -346,6 +379,7 @@ ess_status ess_destroy(ess_ctx *ctx)
         for (auto &kv : c.structures) free_structure(c, *kv.second);
         for (auto &kv : c.volumes) {
             c.free(kv.second->data);
+            c.free(kv.second->cells);
             for (auto &m : kv.second->minmax) c.free(m.second);
         }
         for (auto &kv : c.tfs) {
@@ -363,6 +397,15 @@ ess_status ess_destroy(ess_ctx *ctx)
             cudaEventDestroy(p.b);
         }
         for (auto e : c.free_events) cudaEventDestroy(e);
+        for (auto &kv : c.batch) {
+            Ctx::BatchGroup &g = kv.second;
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            if (g.done) cudaEventDestroy(g.done);
+            if (g.host) cudaFreeHost(g.host);
+            if (g.dev) cudaFree(g.dev);
+        }
+        if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
         cudaFree(c.dev_status);
         cudaFree(c.samples);
         cudaFreeHost(c.host_status);
@@ -401,6 +444,7 @@ ess_status ess_release(ess_ctx *ctx, ess_handle h)
             Volume &v = get_vol(c, h);
             if (v.refs > 0) throw Error{ESS_ERR_ARG, "volume still used by a structure"};
             c.free(v.data);
+            c.free(v.cells);
             for (auto &m : v.minmax) c.free(m.second);
             c.volumes.erase(h);
         } else if (tag == TAG_TF) {
@@ -455,9 +499,22 @@ ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
                 throw Error{ESS_ERR_ARG, msg};
             }
         }
+        // the corner-replicated cells cost 8x the volume; keep them when they
+        // fit in half of the free device memory
+        size_t free_b = 0, total_b = 0;
+        ESS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        if (cell_array_bytes(*v) < free_b / 2) set_sampler(c, *v, 1);
         ess_handle h = new_handle(c, TAG_VOL);
         c.volumes[h] = std::move(v);
         *vol = h;
+    });
+}
+
+ess_status ess_volume_set_sampler(ess_ctx *ctx, ess_handle vol, int cells)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(cells == 0 || cells == 1, "sampler must be 0 (dense) or 1 (cells)");
+        set_sampler(c, get_vol(c, vol), cells);
     });
 }
 
@@ -468,7 +525,7 @@ ess_status ess_tf_set(ess_ctx *ctx, const float *rgba, int on_device, int nt, es
         ESS_REQUIRE(nt >= 2 && nt <= 65536, "nt must be in 2..65536");
         auto t = std::make_unique<TF>();
         t->nt = nt;
-        t->table = (float4 *)c.alloc(sizeof(float4) * nt);
+        t->table = (float4 *)c.alloc(sizeof(float4) * (nt + 1));
         t->prefix = (int *)c.alloc(sizeof(int) * (nt + 1));
         try {
             load_tf(c, *t, rgba, on_device);
@@ -648,16 +705,7 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
 {
     return guard(ctx, [&](Ctx &c) {
         ESS_REQUIRE(camera && params && out, "null pointer");
-        ESS_REQUIRE(W > 0 && H > 0 && W <= 16384 && H <= 16384, "image size must be in 1..16384");
-        ESS_REQUIRE(params->dt >= 1e-3f && params->dt <= 1e4f, "dt must be in [1e-3, 1e4]");
-        ESS_REQUIRE(std::isfinite(params->ert), "ert must be finite");
-        for (int i = 0; i < 3; ++i)
-            ESS_REQUIRE(std::isfinite(camera->eye[i]) && std::isfinite(camera->u[i]) &&
-                            std::isfinite(camera->v[i]) && std::isfinite(camera->w[i]),
-                        "camera must be finite");
-        ESS_REQUIRE(camera->w[0] != 0.0f || camera->w[1] != 0.0f || camera->w[2] != 0.0f ||
-                        !camera->ortho,
-                    "orthographic camera needs a non-zero forward vector");
+        check_render_args(camera, params, W, H);
         Structure &s = get_st(c, structure);
         Volume &v = get_vol(c, s.vol);
         TF &t = get_tf(c, s.tf);
@@ -671,6 +719,7 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
         j.rp = *params;
         j.W = W;
         j.H = H;
+        j.tile_w = params->tile_w;
         size_t bytes = (size_t)W * H * 4 * sizeof(float);
         if (out_on_device) {
             j.out = out;
@@ -686,6 +735,176 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
             ESS_CUDA(cudaMemcpyAsync(out, c.stage, bytes, cudaMemcpyDeviceToHost, c.stream));
             ESS_CUDA(cudaStreamSynchronize(c.stream));
         }
+    });
+}
+
+ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int count, int tile_w)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(items, "null pointer");
+        ESS_REQUIRE(count >= 1 && count <= BATCH_MAX, "batch count must be in 1..4096");
+        ESS_REQUIRE(tile_w == 0 || tile_w == 4 || tile_w == 8 || tile_w == 16 || tile_w == 32,
+                    "tile_w must be 0, 4, 8, 16 or 32");
+        int tw = tile_w ? tile_w : 8;
+        // validate everything before touching the GPU; group by (dtype, kind)
+        std::map<int, std::vector<RenderJob>> groups;
+        for (int i = 0; i < count; ++i) {
+            const ess_render_item &it = items[i];
+            ESS_REQUIRE(it.out, "null output in batch item");
+            check_render_args(&it.camera, &it.params, it.W, it.H);
+            Structure &s = get_st(c, it.structure);
+            Volume &v = get_vol(c, s.vol);
+            TF &t = get_tf(c, s.tf);
+            if (s.tf_version != t.version)
+                throw Error{ESS_ERR_STALE, "batch item structure was built for an older TF table"};
+            RenderJob j;
+            j.vol = &v;
+            j.tf = &t;
+            j.st = &s;
+            j.cam = it.camera;
+            j.rp = it.params;
+            j.W = it.W;
+            j.H = it.H;
+            j.out = it.out;
+            j.tile_w = tw;
+            groups[((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)].push_back(j);
+        }
+        if (!c.capture_stream)
+            ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
+        for (auto &kv : groups) {
+            Ctx::BatchGroup &g = c.batch[kv.first];
+            std::vector<RenderJob> &jobs = kv.second;
+            int n = (int)jobs.size();
+            if (!g.host) {
+                g.cap = batch_bytes(BATCH_MAX);
+                ESS_CUDA(cudaMallocHost(&g.host, g.cap));
+                ESS_CUDA(cudaMalloc(&g.dev, g.cap));
+                ESS_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+                ESS_CUDA(cudaEventRecord(g.done, c.stream));
+            }
+            // the previous replay of this group must have read the staging
+            ESS_CUDA(cudaEventSynchronize(g.done));
+            size_t bytes = pack_batch(c, jobs.data(), n, tw, g.host, g.cap);
+            if (!g.exec) {
+                // capture: copy of the packed batch + the persistent kernel
+                ESS_CUDA(cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal));
+                cudaStream_t saved = c.stream;
+                c.stream = c.capture_stream;
+                cudaError_t e1 = cudaMemcpyAsync(g.dev, g.host, bytes, cudaMemcpyHostToDevice, c.stream);
+                try {
+                    if (e1 == cudaSuccess)
+                        launch_render_batch(c, jobs[0].st->kind, jobs[0].vol->dtype,
+                                            jobs[0].vol->use_cells, g.dev);
+                } catch (...) {
+                    c.stream = saved;
+                    cudaGraph_t tmp;
+                    cudaStreamEndCapture(c.capture_stream, &tmp);
+                    if (tmp) cudaGraphDestroy(tmp);
+                    throw;
+                }
+                c.stream = saved;
+                ESS_CUDA(cudaStreamEndCapture(c.capture_stream, &g.graph));
+                ESS_CUDA(e1);
+                size_t nn = 0;
+                ESS_CUDA(cudaGraphGetNodes(g.graph, nullptr, &nn));
+                std::vector<cudaGraphNode_t> nodes(nn);
+                ESS_CUDA(cudaGraphGetNodes(g.graph, nodes.data(), &nn));
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    ESS_CUDA(cudaGraphNodeGetType(nd, &ty));
+                    if (ty == cudaGraphNodeTypeMemcpy) g.copy_node = nd;
+                }
+                ESS_REQUIRE(g.copy_node, "internal: batch graph has no copy node");
+                ESS_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+            } else {
+                ESS_CUDA(cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.copy_node, g.dev, g.host, bytes,
+                                                            cudaMemcpyHostToDevice));
+            }
+            {
+                Launch L(c, "render_batch");
+                ESS_CUDA(cudaGraphLaunch(g.exec, c.stream));
+            }
+            ESS_CUDA(cudaEventRecord(g.done, c.stream));
+        }
+    });
+}
+
+ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_camera *cameras,
+                        int ncam, const ess_render_params *params, int W, int H,
+                        float frames_per_edit, ess_tune_result *best)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(cameras && params && best && ncam >= 1, "null pointer or no camera");
+        check_render_args(&cameras[0], params, W, H);
+        ESS_REQUIRE(frames_per_edit >= 0.0f, "frames_per_edit must be >= 0");
+        get_vol(c, vol);
+        get_tf(c, tf);
+        float *img = (float *)c.alloc((size_t)W * H * 4 * sizeof(float));
+        cudaEvent_t e0, e1;
+        ESS_CUDA(cudaEventCreate(&e0));
+        ESS_CUDA(cudaEventCreate(&e1));
+        const int kinds[3] = {ESS_GRID, ESS_LBVH, ESS_KD};
+        const int bricks[4] = {4, 8, 16, 32};
+        const int tiles[4] = {4, 8, 16, 32};
+        double best_cost = 1e300;
+        ess_tune_result res{};
+        std::string err;
+        for (int kind : kinds) {
+            for (int B : bricks) {
+                ess_build_params bp{B, 4, 1, 32, 0};
+                ess_handle h = 0;
+                if (ess_build(ctx, vol, tf, (ess_kind)kind, &bp, &h) != ESS_OK) {
+                    c.last_error.clear();
+                    continue;  // e.g. LBVH beyond 1024 bricks per axis
+                }
+                Structure &s = get_st(c, h);
+                // time one rebuild
+                ESS_CUDA(cudaEventRecord(e0, c.stream));
+                run_build(c, s);
+                ESS_CUDA(cudaEventRecord(e1, c.stream));
+                ESS_CUDA(cudaEventSynchronize(e1));
+                float bms = 0.0f;
+                ESS_CUDA(cudaEventElapsedTime(&bms, e0, e1));
+                for (int tw : tiles) {
+                    RenderJob j;
+                    j.vol = &get_vol(c, vol);
+                    j.tf = &get_tf(c, tf);
+                    j.st = &s;
+                    j.rp = *params;
+                    j.W = W;
+                    j.H = H;
+                    j.out = img;
+                    j.tile_w = tw;
+                    j.cam = cameras[0];
+                    launch_render(c, j);  // warm-up
+                    ESS_CUDA(cudaEventRecord(e0, c.stream));
+                    for (int k = 0; k < ncam; ++k) {
+                        j.cam = cameras[k];
+                        launch_render(c, j);
+                    }
+                    ESS_CUDA(cudaEventRecord(e1, c.stream));
+                    ESS_CUDA(cudaEventSynchronize(e1));
+                    float rms = 0.0f;
+                    ESS_CUDA(cudaEventElapsedTime(&rms, e0, e1));
+                    rms /= (float)ncam;
+                    double cost = bms + (double)frames_per_edit * rms;
+                    if (cost < best_cost) {
+                        best_cost = cost;
+                        res.kind = kind;
+                        res.brick = B;
+                        res.tile_w = tw;
+                        res.build_ms = bms;
+                        res.render_ms = rms;
+                    }
+                }
+                ess_release(ctx, h);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.free(img);
+        ESS_REQUIRE(best_cost < 1e300, "autotune: no candidate could be built");
+        *best = res;
     });
 }
 

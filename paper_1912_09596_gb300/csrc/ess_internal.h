@@ -64,6 +64,9 @@ struct Volume {
     float value_lo, value_hi;
     void *data = nullptr;   // device copy, x fastest
     size_t bytes = 0;
+    void *cells = nullptr;  // corner-replicated trilinear cells, (n+1)^3 x 8 values
+    size_t cell_bytes = 0;
+    bool use_cells = false;
     std::map<int, float2 *> minmax;  // per brick size: apron min/max (cached)
     int refs = 0;           // structures using the volume
     bool released = false;
@@ -153,6 +156,19 @@ struct Ctx {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_events;
     std::map<std::string, std::pair<uint64_t, double>> prof;
+    // batched rendering: one captured graph per (dtype, kind) group
+    struct BatchGroup {
+        void *host = nullptr;       // pinned staging
+        void *dev = nullptr;        // device copy
+        size_t cap = 0;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t copy_node = nullptr;
+        cudaEvent_t done = nullptr;  // last replay finished reading the staging
+        int n_captured = -1;
+    };
+    std::map<int, BatchGroup> batch;
+    cudaStream_t capture_stream = nullptr;
 
     void *alloc(size_t bytes);
     void free(void *p);
@@ -174,6 +190,8 @@ struct Launch {
 // ----------------------------------------------------------- launchers
 // classify.cu
 void launch_check_finite(Ctx &c, const float *v, size_t n);
+size_t cell_array_bytes(const Volume &v);
+void launch_build_cells(Ctx &c, const Volume &v, void *cells);
 void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out);
 void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, int validate);
 void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf,
@@ -206,7 +224,16 @@ struct RenderJob {
     ess_render_params rp;
     int W, H;
     float *out;  // device, W*H*4
+    int tile_w = 8;  // warp tile width in pixels (4, 8, 16 or 32)
 };
 void launch_render(Ctx &c, const RenderJob &job);
+constexpr int BATCH_MAX = 4096;
+size_t batch_bytes(int n);
+size_t pack_batch(Ctx &c, const RenderJob *jobs, int n, int tw, void *host, size_t cap);
+void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, void *dev);
 
 }  // namespace ess
+
+struct ess_ctx {
+    ess::Ctx c;
+};

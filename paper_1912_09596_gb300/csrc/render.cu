@@ -22,6 +22,7 @@ namespace ess {
 
 struct RArgs {
     const void *vol;
+    const void *cells;   // corner-replicated cells (nullptr: dense sampling only)
     int nx, ny, nz;
     float value_lo, s;   // TF coordinate x = (v - value_lo) * s
     const float4 *tf;
@@ -103,30 +104,90 @@ template <typename T> __device__ __forceinline__ float ldv(const T *p) { return 
 
 __device__ __forceinline__ float lerpf(float a, float b, float f) { return fmaf(f, b - a, a); }
 
-template <typename T>
+// The 8 corner values of trilinear cell (ix, iy, iz) (i0 = floor(p - 0.5)),
+// neighbours clamped to the volume, in the order 000 100 010 110 001 101 011 111.
+// Dense sampling reads them from the volume (8 loads); cell sampling reads
+// the copy that the cell array keeps of exactly those values (one vector
+// load): cell (cx, cy, cz) = (ix + 1, iy + 1, iz + 1), 0 <= c <= n.
+template <typename T, int SAMPLER> struct Corners;
+
+template <typename T> struct Corners<T, 0> {
+    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+    {
+        const T *vol = (const T *)a.vol;
+        int x0 = min(max(ix, 0), a.nx - 1), x1 = min(max(ix + 1, 0), a.nx - 1);
+        int y0 = min(max(iy, 0), a.ny - 1), y1 = min(max(iy + 1, 0), a.ny - 1);
+        int z0 = min(max(iz, 0), a.nz - 1), z1 = min(max(iz + 1, 0), a.nz - 1);
+        size_t r00 = (size_t)(z0 * a.ny + y0) * (size_t)a.nx, r10 = (size_t)(z0 * a.ny + y1) * (size_t)a.nx;
+        size_t r01 = (size_t)(z1 * a.ny + y0) * (size_t)a.nx, r11 = (size_t)(z1 * a.ny + y1) * (size_t)a.nx;
+        v[0] = ldv(vol + r00 + x0);
+        v[1] = ldv(vol + r00 + x1);
+        v[2] = ldv(vol + r10 + x0);
+        v[3] = ldv(vol + r10 + x1);
+        v[4] = ldv(vol + r01 + x0);
+        v[5] = ldv(vol + r01 + x1);
+        v[6] = ldv(vol + r11 + x0);
+        v[7] = ldv(vol + r11 + x1);
+    }
+};
+
+__device__ __forceinline__ size_t cell_index(const RArgs &a, int ix, int iy, int iz)
+{
+    int cx = min(max(ix + 1, 0), a.nx), cy = min(max(iy + 1, 0), a.ny), cz = min(max(iz + 1, 0), a.nz);
+    return (size_t)(cz * (a.ny + 1) + cy) * (size_t)(a.nx + 1) + cx;
+}
+
+template <> struct Corners<uint8_t, 1> {
+    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+    {
+        uint2 c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_index(a, ix, iy, iz));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (float)((c.x >> (8 * k)) & 0xffu);
+            v[4 + k] = (float)((c.y >> (8 * k)) & 0xffu);
+        }
+    }
+};
+
+template <> struct Corners<uint16_t, 1> {
+    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+    {
+        uint4 c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_index(a, ix, iy, iz));
+        uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = (float)(w[k] & 0xffffu);
+            v[2 * k + 1] = (float)(w[k] >> 16);
+        }
+    }
+};
+
+template <> struct Corners<float, 1> {
+    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(a.cells) + 2 * cell_index(a, ix, iy, iz);
+        float4 c0 = __ldg(p), c1 = __ldg(p + 1);
+        v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w;
+        v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
+    }
+};
+
+template <typename T, int SAMPLER>
 __device__ __forceinline__ float sample_value(const RArgs &a, float px, float py, float pz)
 {
-    const T *vol = (const T *)a.vol;
     float qx = px - 0.5f, qy = py - 0.5f, qz = pz - 0.5f;
     float gxf = floorf(qx), gyf = floorf(qy), gzf = floorf(qz);
-    int ix = (int)gxf, iy = (int)gyf, iz = (int)gzf;
     float fx = qx - gxf, fy = qy - gyf, fz = qz - gzf;
-    int x0 = min(max(ix, 0), a.nx - 1), x1 = min(max(ix + 1, 0), a.nx - 1);
-    int y0 = min(max(iy, 0), a.ny - 1), y1 = min(max(iy + 1, 0), a.ny - 1);
-    int z0 = min(max(iz, 0), a.nz - 1), z1 = min(max(iz + 1, 0), a.nz - 1);
-    size_t sy = (size_t)a.nx, sz = (size_t)a.nx * (size_t)a.ny;
-    size_t r00 = z0 * sz + y0 * sy, r10 = z0 * sz + y1 * sy;
-    size_t r01 = z1 * sz + y0 * sy, r11 = z1 * sz + y1 * sy;
-    float v000 = ldv(vol + r00 + x0), v100 = ldv(vol + r00 + x1);
-    float v010 = ldv(vol + r10 + x0), v110 = ldv(vol + r10 + x1);
-    float v001 = ldv(vol + r01 + x0), v101 = ldv(vol + r01 + x1);
-    float v011 = ldv(vol + r11 + x0), v111 = ldv(vol + r11 + x1);
-    float c00 = lerpf(v000, v100, fx), c10 = lerpf(v010, v110, fx);
-    float c01 = lerpf(v001, v101, fx), c11 = lerpf(v011, v111, fx);
+    float v[8];
+    Corners<T, SAMPLER>::get(a, (int)gxf, (int)gyf, (int)gzf, v);
+    float c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+    float c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
     float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
     return lerpf(c0, c1, fz);
 }
 
+// The table holds nt + 1 entries, the last a copy of entry nt - 1, so that
+// entry i0 + 1 needs no clamp (with x = nt - 1 the weight w is 0 anyway).
 __device__ __forceinline__ float4 classify(const RArgs &a, float v)
 {
     float x = (v - a.value_lo) * a.s;
@@ -134,19 +195,18 @@ __device__ __forceinline__ float4 classify(const RArgs &a, float v)
     x = x < 0.0f ? 0.0f : x;
     x = x > xmax ? xmax : x;
     int i0 = (int)x;
-    int i1 = i0 + 1 < a.nt ? i0 + 1 : a.nt - 1;
     float w = x - (float)i0;
-    float4 c0 = __ldg(a.tf + i0), c1 = __ldg(a.tf + i1);
+    float4 c0 = __ldg(a.tf + i0), c1 = __ldg(a.tf + i0 + 1);
     return make_float4(fmaf(w, c1.x - c0.x, c0.x), fmaf(w, c1.y - c0.y, c0.y),
                        fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
 }
 
 // One sample (R6 compositing, R7 early termination); true when A >= ert.
-template <typename T>
+template <typename T, int SAMPLER>
 __device__ __forceinline__ bool sample_step(const RArgs &a, const Ray &r, float t, Acc &acc)
 {
     float px = fmaf(t, r.d[0], r.o[0]), py = fmaf(t, r.d[1], r.o[1]), pz = fmaf(t, r.d[2], r.o[2]);
-    float4 c = classify(a, sample_value<T>(a, px, py, pz));
+    float4 c = classify(a, sample_value<T, SAMPLER>(a, px, py, pz));
     float tr = (1.0f - acc.a) * c.w;
     acc.r = fmaf(tr, c.x, acc.r);
     acc.g = fmaf(tr, c.y, acc.g);
@@ -155,8 +215,10 @@ __device__ __forceinline__ bool sample_step(const RArgs &a, const Ray &r, float 
     return acc.a >= a.ert;
 }
 
-// Rule S over one hit interval; returns true when the ray is finished.
-template <typename T>
+// Rule S over one hit interval; returns true when the ray is finished.  The
+// loop counter is kept as a float as well (exact below 2^24), which is the
+// value (float)k.
+template <typename T, int SAMPLER>
 __device__ __forceinline__ bool march(const RArgs &a, const Ray &r, float tn, float tf, float ta,
                                       float tb, int &k_next, Acc &acc, long long &ns)
 {
@@ -165,26 +227,28 @@ __device__ __forceinline__ bool march(const RArgs &a, const Ray &r, float tn, fl
     kb = kb < 16777216.0f ? kb : 16777216.0f;
     int k0 = ka > (float)k_next ? (int)ka : k_next;
     int k1 = (int)kb;
-    for (int k = k0; k <= k1; ++k) {
-        float t = fmaf((float)k, a.dt, tn);
+    float kf = (float)k0;
+    for (int k = k0; k <= k1; ++k, kf += 1.0f) {
+        float t = fmaf(kf, a.dt, tn);
         if (!(t < tf)) return true;
         ++ns;
-        if (sample_step<T>(a, r, t, acc)) return true;
+        if (sample_step<T, SAMPLER>(a, r, t, acc)) return true;
     }
     if (k1 + 1 > k_next) k_next = k1 + 1;
     return false;
 }
 
 // ------------------------------------------------------------- traversals
-template <typename T>
+template <typename T, int SAMPLER>
 __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float tn, float tf,
                                             Acc &acc, long long &ns)
 {
-    for (int k = 0;; ++k) {
-        float t = fmaf((float)k, a.dt, tn);
+    float kf = 0.0f;
+    for (int k = 0; k < 16777216; ++k, kf += 1.0f) {
+        float t = fmaf(kf, a.dt, tn);
         if (!(t < tf)) break;
         ++ns;
-        if (sample_step<T>(a, r, t, acc)) break;
+        if (sample_step<T, SAMPLER>(a, r, t, acc)) break;
     }
 }
 
@@ -192,54 +256,61 @@ __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float 
 // ray order; for a non-empty cell the exact slab interval of its box is
 // marched.  Boundary crossings are recomputed from integer plane positions
 // (no drift) and every axis only moves one way, so at most gx+gy+gz steps.
-template <typename T>
+// All state is in scalar registers.
+__device__ __forceinline__ void dda_axis(float o, float d, float inv, bool zero, float p, int B,
+                                         int g, int &c, int &step, float &tnext)
+{
+    c = (int)floorf(p / (float)B);
+    c = min(max(c, 0), g - 1);
+    if (zero) {
+        step = 0;
+        tnext = INFINITY;
+    } else if (d > 0.0f) {
+        step = 1;
+        tnext = ((float)((c + 1) * B) - o) * inv;
+    } else {
+        step = -1;
+        tnext = ((float)(c * B) - o) * inv;
+    }
+}
+
+template <typename T, int SAMPLER>
 __device__ __forceinline__ void trace_grid(const RArgs &a, const Ray &r, float tn, float tf,
                                            Acc &acc, long long &ns)
 {
-    const int g[3] = {a.gx, a.gy, a.gz};
-    const int n[3] = {a.nx, a.ny, a.nz};
-    const float Bf = (float)a.B;
-    int cell[3], step[3];
-    float tnext[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        float p = fmaf(tn, r.d[ax], r.o[ax]);
-        int c = (int)floorf(p / Bf);
-        c = min(max(c, 0), g[ax] - 1);
-        cell[ax] = c;
-        if (r.zero[ax]) {
-            step[ax] = 0;
-            tnext[ax] = INFINITY;
-        } else if (r.d[ax] > 0.0f) {
-            step[ax] = 1;
-            tnext[ax] = ((float)((c + 1) * a.B) - r.o[ax]) * r.inv[ax];
-        } else {
-            step[ax] = -1;
-            tnext[ax] = ((float)(c * a.B) - r.o[ax]) * r.inv[ax];
-        }
-    }
+    const int B = a.B;
+    int cx, cy, cz, sx, sy, sz;
+    float tx, ty, tz;
+    dda_axis(r.o[0], r.d[0], r.inv[0], r.zero[0], fmaf(tn, r.d[0], r.o[0]), B, a.gx, cx, sx, tx);
+    dda_axis(r.o[1], r.d[1], r.inv[1], r.zero[1], fmaf(tn, r.d[1], r.o[1]), B, a.gy, cy, sy, ty);
+    dda_axis(r.o[2], r.d[2], r.inv[2], r.zero[2], fmaf(tn, r.d[2], r.o[2]), B, a.gz, cz, sz, tz);
     int k_next = 0;
-    int maxit = g[0] + g[1] + g[2] + 3;
+    const int maxit = a.gx + a.gy + a.gz + 3;
     for (int it = 0; it < maxit; ++it) {
-        size_t id = ((size_t)cell[2] * a.gy + cell[1]) * a.gx + cell[0];
-        if (__ldg(a.mask + id)) {
-            float lo[3], hi[3];
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                lo[ax] = (float)(cell[ax] * a.B);
-                hi[ax] = (float)min((cell[ax] + 1) * a.B, n[ax]);
-            }
+        if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
+            float lo[3] = {(float)(cx * B), (float)(cy * B), (float)(cz * B)};
+            float hi[3] = {(float)min((cx + 1) * B, a.nx), (float)min((cy + 1) * B, a.ny),
+                           (float)min((cz + 1) * B, a.nz)};
             float ta = tn, tb = tf;
             slab(r, lo, hi, ta, tb);
-            if (ta <= tb && march<T>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
+            if (ta <= tb && march<T, SAMPLER>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
         }
-        int ax = 0;
-        if (tnext[1] < tnext[ax]) ax = 1;
-        if (tnext[2] < tnext[ax]) ax = 2;
-        if (!(tnext[ax] <= tf)) return;
-        cell[ax] += step[ax];
-        if (cell[ax] < 0 || cell[ax] >= g[ax]) return;
-        tnext[ax] = ((float)((cell[ax] + (step[ax] > 0 ? 1 : 0)) * a.B) - r.o[ax]) * r.inv[ax];
+        if (tx <= ty && tx <= tz) {
+            if (!(tx <= tf)) return;
+            cx += sx;
+            if (cx < 0 || cx >= a.gx) return;
+            tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
+        } else if (ty <= tz) {
+            if (!(ty <= tf)) return;
+            cy += sy;
+            if (cy < 0 || cy >= a.gy) return;
+            ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
+        } else {
+            if (!(tz <= tf)) return;
+            cz += sz;
+            if (cz < 0 || cz >= a.gz) return;
+            tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
+        }
     }
 }
 
@@ -277,7 +348,7 @@ __device__ __forceinline__ void leaf_box_f(const RArgs &a, int KIND, int32_t ref
 // front-to-back order).  A leaf's box interval is marched with rule S.  The
 // stack of STACK entries suffices because the build guarantees a height of at
 // most STACK + 1 levels (30-bit Morton keys give LBVH heights <= 31).
-template <typename T, int KIND, int STACK>
+template <typename T, int SAMPLER, int KIND, int STACK>
 __device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float tn, float tf,
                                            Acc &acc, long long &ns)
 {
@@ -308,7 +379,7 @@ __device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float t
             leaf_box_f(a, KIND, ref, lo, hi);
             float ta = tn, tb = tf;
             slab(r, lo, hi, ta, tb);
-            if (ta <= tb && march<T>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
+            if (ta <= tb && march<T, SAMPLER>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
         } else {
             if (ref >= n_inner) return;
             const uint4 *q = reinterpret_cast<const uint4 *>(a.nodes + ref);
@@ -344,58 +415,136 @@ __device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float t
     }
 }
 
-// ------------------------------------------------------------------ kernel
-// 128 threads per block, 16 x 8 pixels; each warp covers an 8 x 4 tile so
-// that its rays stay close together.
-template <typename T, int KIND>
-__global__ void __launch_bounds__(128) k_render(RArgs a)
+// ------------------------------------------------------------------ kernels
+// One pixel: ray, volume interval, traversal of the structure, background.
+// Shared by the plain and the batched kernels, so both give the same bits.
+template <typename T, int SAMPLER, int KIND>
+__device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long long &ns)
+{
+    Ray r;
+    gen_ray(a, x, y, r);
+    float lo[3] = {0.0f, 0.0f, 0.0f};
+    float hi[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
+    float tn = 0.0f, tf = INFINITY;
+    slab(r, lo, hi, tn, tf);
+    Acc acc = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (tn < tf) {
+        if (KIND == ESS_NONE)
+            trace_naive<T, SAMPLER>(a, r, tn, tf, acc, ns);
+        else if (KIND == ESS_GRID)
+            trace_grid<T, SAMPLER>(a, r, tn, tf, acc, ns);
+        else if (KIND == ESS_LBVH)
+            trace_tree<T, SAMPLER, ESS_LBVH, 32>(a, r, tn, tf, acc, ns);
+        else
+            trace_tree<T, SAMPLER, ESS_KD, 128>(a, r, tn, tf, acc, ns);
+    }
+    float one_m = 1.0f - acc.a;
+    a.out[(size_t)y * a.W + x] =
+        make_float4(fmaf(one_m, a.bg[0], acc.r), fmaf(one_m, a.bg[1], acc.g),
+                    fmaf(one_m, a.bg[2], acc.b), fmaf(one_m, a.bg[3], acc.a));
+}
+
+// A block is 4 warps arranged 2 x 2; a warp covers a tw x (32/tw) pixel tile
+// (tw in {4, 8, 16, 32}) so that its rays stay close together.  The block
+// covers (2 tw) x (64/tw) pixels.
+__device__ __forceinline__ void block_pixel(int tw, int bx, int by, int &x, int &y)
 {
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    int y = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    long long ns = 0;
-    if (x < a.W && y < a.H) {
-        Ray r;
-        gen_ray(a, x, y, r);
-        float lo[3] = {0.0f, 0.0f, 0.0f};
-        float hi[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
-        float tn = 0.0f, tf = INFINITY;
-        slab(r, lo, hi, tn, tf);
-        Acc acc = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (tn < tf) {
-            if (KIND == ESS_NONE)
-                trace_naive<T>(a, r, tn, tf, acc, ns);
-            else if (KIND == ESS_GRID)
-                trace_grid<T>(a, r, tn, tf, acc, ns);
-            else if (KIND == ESS_LBVH)
-                trace_tree<T, ESS_LBVH, 32>(a, r, tn, tf, acc, ns);
-            else
-                trace_tree<T, ESS_KD, 128>(a, r, tn, tf, acc, ns);
-        }
-        float one_m = 1.0f - acc.a;
-        a.out[(size_t)y * a.W + x] =
-            make_float4(fmaf(one_m, a.bg[0], acc.r), fmaf(one_m, a.bg[1], acc.g),
-                        fmaf(one_m, a.bg[2], acc.b), fmaf(one_m, a.bg[3], acc.a));
-    }
+    int th = 32 / tw;
+    x = bx * 2 * tw + (warp & 1) * tw + (lane % tw);
+    y = by * 2 * th + (warp >> 1) * th + (lane / tw);
+}
+
+__device__ __forceinline__ void count_samples(unsigned long long *samples, long long ns)
+{
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ns += __shfl_xor_sync(0xffffffffu, ns, o);
-    if (lane == 0 && ns) atomicAdd(a.samples, (unsigned long long)ns);
+    if ((threadIdx.x & 31) == 0 && ns) atomicAdd(samples, (unsigned long long)ns);
 }
 
-template <int KIND> static void launch_kind(Ctx &c, const RArgs &a, ess_dtype dt)
+template <typename T, int SAMPLER, int KIND>
+__global__ void __launch_bounds__(128) k_render(RArgs a, int tw)
 {
-    dim3 grid((a.W + 15) / 16, (a.H + 7) / 8);
+    int x, y;
+    block_pixel(tw, blockIdx.x, blockIdx.y, x, y);
+    long long ns = 0;
+    if (x < a.W && y < a.H) render_pixel<T, SAMPLER, KIND>(a, x, y, ns);
+    count_samples(a.samples, ns);
+}
+
+// Persistent batched render: every block repeatedly takes the next tile of
+// the work list (an atomic counter), finds its image by binary search over the
+// per-image tile prefix, and renders it.  Images of any size and count share
+// one launch; the dynamic tile order balances uneven work.
+struct BatchHeader {
+    int nitems, total_tiles, tile_counter, tw;
+};
+
+template <typename T, int SAMPLER, int KIND>
+__global__ void __launch_bounds__(128) k_render_batch(const RArgs *__restrict__ items,
+                                                      const int *__restrict__ tile_prefix,
+                                                      BatchHeader *hdr)
+{
+    __shared__ RArgs sa;
+    __shared__ int s_tile, s_item;
+    const int nitems = hdr->nitems, total = hdr->total_tiles, tw = hdr->tw;
+    const int bw = 2 * tw, bh = 64 / tw;
+    long long ns = 0;
+    while (true) {
+        if (threadIdx.x == 0) {
+            int t = atomicAdd(&hdr->tile_counter, 1);
+            s_tile = t;
+            int lo = 0, hi = nitems - 1;  // last item with prefix <= t
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (tile_prefix[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            s_item = lo;
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= total) break;
+        {
+            const int *src = reinterpret_cast<const int *>(items + s_item);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int k = threadIdx.x; k < (int)(sizeof(RArgs) / 4); k += blockDim.x) dst[k] = src[k];
+        }
+        __syncthreads();
+        int local = tile - tile_prefix[s_item];
+        int tiles_x = (sa.W + bw - 1) / bw;
+        int x, y;
+        block_pixel(tw, local % tiles_x, local / tiles_x, x, y);
+        (void)bh;
+        if (x < sa.W && y < sa.H) render_pixel<T, SAMPLER, KIND>(sa, x, y, ns);
+        __syncthreads();
+    }
+    count_samples(items[0].samples, ns);
+}
+
+template <int KIND> static void launch_kind(Ctx &c, const RArgs &a, ess_dtype dt, int tw)
+{
+    dim3 grid((a.W + 2 * tw - 1) / (2 * tw), (a.H + 64 / tw - 1) / (64 / tw));
+    bool cells = a.cells != nullptr;
     switch (dt) {
-    case ESS_U8: k_render<uint8_t, KIND><<<grid, 128, 0, c.stream>>>(a); break;
-    case ESS_U16: k_render<uint16_t, KIND><<<grid, 128, 0, c.stream>>>(a); break;
-    default: k_render<float, KIND><<<grid, 128, 0, c.stream>>>(a); break;
+    case ESS_U8:
+        if (cells) k_render<uint8_t, 1, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        else k_render<uint8_t, 0, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        break;
+    case ESS_U16:
+        if (cells) k_render<uint16_t, 1, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        else k_render<uint16_t, 0, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        break;
+    default:
+        if (cells) k_render<float, 1, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        else k_render<float, 0, KIND><<<grid, 128, 0, c.stream>>>(a, tw);
+        break;
     }
 }
 
-void launch_render(Ctx &c, const RenderJob &j)
+static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
 {
-    RArgs a;
     a.vol = j.vol->data;
+    a.cells = j.vol->use_cells ? j.vol->cells : nullptr;
     a.nx = j.vol->nx;
     a.ny = j.vol->ny;
     a.nz = j.vol->nz;
@@ -426,29 +575,111 @@ void launch_render(Ctx &c, const RenderJob &j)
     a.count = j.st->kind == ESS_KD ? j.st->kd_count_dev : j.st->count;
     a.kd_nodes = j.st->kd_nodes;
     a.samples = c.samples;
+}
+
+static const char *render_name(int kind)
+{
+    switch (kind) {
+    case ESS_NONE: return "render_naive";
+    case ESS_GRID: return "render_grid";
+    case ESS_LBVH: return "render_lbvh";
+    default: return "render_kd";
+    }
+}
+
+static int tile_width(int w)
+{
+    return (w == 4 || w == 8 || w == 16 || w == 32) ? w : 8;
+}
+
+void launch_render(Ctx &c, const RenderJob &j)
+{
+    RArgs a;
+    fill_args(c, j, a);
+    int tw = tile_width(j.tile_w);
+    Launch L(c, render_name(j.st->kind));
     switch (j.st->kind) {
-    case ESS_NONE: {
-        Launch L(c, "render_naive");
-        launch_kind<ESS_NONE>(c, a, j.vol->dtype);
-        break;
+    case ESS_NONE: launch_kind<ESS_NONE>(c, a, j.vol->dtype, tw); break;
+    case ESS_GRID: launch_kind<ESS_GRID>(c, a, j.vol->dtype, tw); break;
+    case ESS_LBVH: launch_kind<ESS_LBVH>(c, a, j.vol->dtype, tw); break;
+    default: launch_kind<ESS_KD>(c, a, j.vol->dtype, tw); break;
     }
-    case ESS_GRID: {
-        Launch L(c, "render_grid");
-        launch_kind<ESS_GRID>(c, a, j.vol->dtype);
-        break;
+}
+
+// ------------------------------------------------------------ batched path
+size_t batch_args_bytes() { return sizeof(RArgs); }
+
+// Batch layout (fixed offsets, so that a captured launch stays valid for any
+// item count): header, tile prefix (BATCH_MAX + 1 ints, 16-byte padded), then
+// BATCH_MAX RArgs.
+static size_t batch_prefix_bytes() { return ((sizeof(int) * (BATCH_MAX + 1)) + 15) & ~(size_t)15; }
+
+size_t batch_bytes(int n) { return sizeof(BatchHeader) + batch_prefix_bytes() + sizeof(RArgs) * n; }
+
+// Packs the jobs of one (dtype, kind) group into `host` (pinned).  Returns the
+// number of bytes to copy to the device.
+size_t pack_batch(Ctx &c, const RenderJob *jobs, int n, int tw, void *host, size_t cap)
+{
+    size_t prefix_bytes = batch_prefix_bytes();
+    size_t need = batch_bytes(n);
+    if (need > cap) throw Error{ESS_ERR_ARG, "render batch too large for the staging buffer"};
+    char *p = (char *)host;
+    BatchHeader *h = (BatchHeader *)p;
+    int *prefix = (int *)(p + sizeof(BatchHeader));
+    RArgs *args = (RArgs *)(p + sizeof(BatchHeader) + prefix_bytes);
+    int bw = 2 * tw, bh = 64 / tw;
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        prefix[i] = acc;
+        acc += ((jobs[i].W + bw - 1) / bw) * ((jobs[i].H + bh - 1) / bh);
+        fill_args(c, jobs[i], args[i]);
     }
-    case ESS_LBVH: {
-        Launch L(c, "render_lbvh");
-        launch_kind<ESS_LBVH>(c, a, j.vol->dtype);
-        break;
+    prefix[n] = acc;
+    h->nitems = n;
+    h->total_tiles = acc;
+    h->tile_counter = 0;
+    h->tw = tw;
+    return need;
+}
+
+// Persistent launch over a packed batch already copied to `dev` (same
+// layout).  Grid: every SM filled to its occupancy.
+void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, void *dev)
+{
+    size_t prefix_bytes = batch_prefix_bytes();
+    char *p = (char *)dev;
+    BatchHeader *h = (BatchHeader *)p;
+    const int *prefix = (const int *)(p + sizeof(BatchHeader));
+    const RArgs *args = (const RArgs *)(p + sizeof(BatchHeader) + prefix_bytes);
+    int sms = 0, per_sm = 0;
+    ESS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+#define ESS_BATCH_S(T, S, K)                                                                  \
+    do {                                                                                      \
+        ESS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch<T, S, K>, \
+                                                               128, 0));                      \
+        k_render_batch<T, S, K><<<sms * (per_sm > 0 ? per_sm : 1), 128, 0, c.stream>>>(args,    \
+                                                                                   prefix, h); \
+    } while (0)
+#define ESS_BATCH(T, K)                        \
+    do {                                       \
+        if (cells) ESS_BATCH_S(T, 1, K);       \
+        else ESS_BATCH_S(T, 0, K);             \
+    } while (0)
+#define ESS_BATCH_T(K)                                   \
+    switch (dt) {                                        \
+    case ESS_U8: ESS_BATCH(uint8_t, K); break;           \
+    case ESS_U16: ESS_BATCH(uint16_t, K); break;         \
+    default: ESS_BATCH(float, K); break;                 \
     }
-    case ESS_KD: {
-        Launch L(c, "render_kd");
-        launch_kind<ESS_KD>(c, a, j.vol->dtype);
-        break;
+    switch (kind) {
+    case ESS_NONE: ESS_BATCH_T(ESS_NONE); break;
+    case ESS_GRID: ESS_BATCH_T(ESS_GRID); break;
+    case ESS_LBVH: ESS_BATCH_T(ESS_LBVH); break;
+    default: ESS_BATCH_T(ESS_KD); break;
     }
-    default: throw Error{ESS_ERR_ARG, "render: structure kind not supported"};
-    }
+#undef ESS_BATCH_T
+#undef ESS_BATCH
+#undef ESS_BATCH_S
 }
 
 }  // namespace ess

@@ -49,7 +49,37 @@ class Camera(C.Structure):
 
 
 class RenderParams(C.Structure):
-    _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4)]
+    _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4),
+                ("tile_w", C.c_int)]
+
+
+class RenderItem(C.Structure):
+    _fields_ = [("structure", C.c_uint64), ("camera", Camera), ("params", RenderParams),
+                ("W", C.c_int), ("H", C.c_int), ("out", C.c_void_p)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("memory_budget", C.c_size_t), ("max_batch", C.c_int),
+                ("max_inflight", C.c_int), ("tile_w", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("structure", C.c_uint64), ("rgba", C.c_void_p),
+                ("nt", C.c_int), ("camera", Camera), ("params", RenderParams),
+                ("W", C.c_int), ("H", C.c_int), ("out", C.c_void_p)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("queue_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+REQ_RENDER, REQ_EDIT = 0, 1
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("kind", C.c_int), ("brick", C.c_int), ("tile_w", C.c_int),
+                ("build_ms", C.c_float), ("render_ms", C.c_float)]
 
 
 class StructureInfo(C.Structure):
@@ -72,6 +102,7 @@ def _load():
         "ess_release": [vp, h],
         "ess_volume_upload": [vp, vp, i, i, i, i, i, f, f, P(h)],
         "ess_tf_set": [vp, vp, i, i, P(h)],
+        "ess_volume_set_sampler": [vp, h, i],
         "ess_tf_update": [vp, h, vp, i, i],
         "ess_build": [vp, h, h, i, P(BuildParams), P(h)],
         "ess_rebuild": [vp, h],
@@ -83,6 +114,14 @@ def _load():
         "ess_profile_read": [vp, i, P(C.c_char_p), P(C.c_uint64), P(C.c_double), P(i)],
         "ess_profile_reset": [vp],
         "ess_compact_mask_noalloc": [vp, C.c_int64, vp, vp, vp],
+        "ess_render_batch": [vp, P(RenderItem), i, i],
+        "ess_server_create": [vp, P(ServerConfig), P(vp)],
+        "ess_server_submit": [vp, P(Request), P(C.c_uint64)],
+        "ess_server_poll": [vp, C.c_uint64, P(RequestStatus)],
+        "ess_server_wait": [vp, C.c_uint64, P(RequestStatus)],
+        "ess_server_drain": [vp],
+        "ess_server_destroy": [vp],
+        "ess_autotune": [vp, h, h, P(Camera), i, P(RenderParams), i, i, f, P(TuneResult)],
     }
     for name, args in sigs.items():
         fn = getattr(L, name)
@@ -159,6 +198,10 @@ def ess_volume_upload(ctx, data, value_lo, value_hi):
     return h.value
 
 
+def ess_volume_set_sampler(ctx, vol, cells):
+    _check(ctx, lib.ess_volume_set_sampler(ctx, vol, int(cells)))
+
+
 def ess_tf_set(ctx, rgba):
     """`rgba`: (nt, 4) float32 array or tensor."""
     p, dev = _ptr(rgba)
@@ -225,12 +268,13 @@ def camera_from(cam):
     return camera(cam.eye, cam.u, cam.v, cam.w, cam.ortho)
 
 
-def render_params(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0)):
+def render_params(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), tile_w=0):
     p = RenderParams()
     p.dt = dt
     p.ert = ert
     for i in range(4):
         p.bg[i] = float(bg[i])
+    p.tile_w = int(tile_w)
     return p
 
 
@@ -252,6 +296,83 @@ def ess_compact_mask_noalloc(mask, ids, count, stream=None):
                                       _ptr(count)[0], C.c_void_p(raw) if raw else None)
     if st != OK:
         raise EssError(st, "ess_compact_mask_noalloc failed")
+
+
+def ess_render_batch(ctx, items, tile_w=0):
+    """`items`: list of (structure, camera, params, W, H, out CUDA tensor)."""
+    arr = (RenderItem * len(items))()
+    for k, (st, cam, params, W, H, out) in enumerate(items):
+        if not isinstance(cam, Camera):
+            cam = camera_from(cam)
+        p, dev = _ptr(out)
+        if not dev:
+            raise ValueError("batched outputs must be device memory")
+        arr[k] = RenderItem(st, cam, params, W, H, p)
+    _check(ctx, lib.ess_render_batch(ctx, arr, len(items), int(tile_w)))
+
+
+def ess_autotune(ctx, vol, tf, cameras, params, W, H, frames_per_edit=1.0):
+    cams = (Camera * len(cameras))(*[c if isinstance(c, Camera) else camera_from(c)
+                                      for c in cameras])
+    res = TuneResult()
+    _check(ctx, lib.ess_autotune(ctx, vol, tf, cams, len(cameras), C.byref(params), W, H,
+                                 float(frames_per_edit), C.byref(res)))
+    return {k: getattr(res, k) for k, _ in TuneResult._fields_}
+
+
+def ess_server_create(ctx, memory_budget=0, max_batch=256, max_inflight=2, tile_w=0):
+    srv = C.c_void_p()
+    cfg = ServerConfig(memory_budget, max_batch, max_inflight, tile_w)
+    st = lib.ess_server_create(ctx, C.byref(cfg), C.byref(srv))
+    if st != OK:
+        raise EssError(st, "ess_server_create failed")
+    return srv
+
+
+def ess_server_submit(srv, kind, structure, cam, params, W, H, out, rgba=None):
+    """`out`: host float32 (H, W, 4) numpy array or pinned tensor that stays
+    alive until the request is done; `rgba`: (nt, 4) host table for an edit."""
+    if not isinstance(cam, Camera):
+        cam = camera_from(cam)
+    p_out, dev = _ptr(out)
+    if dev:
+        raise ValueError("server outputs are host memory")
+    p_tf, nt = (None, 0)
+    if rgba is not None:
+        p_tf, _ = _ptr(rgba)
+        nt = int(rgba.shape[0])
+    req = Request(kind, structure, p_tf, nt, cam, params, W, H, p_out)
+    rid = C.c_uint64()
+    st = lib.ess_server_submit(srv, C.byref(req), C.byref(rid))
+    if st != OK:
+        raise EssError(st, "ess_server_submit failed")
+    return rid.value
+
+
+def _status(fn, srv, rid):
+    s = RequestStatus()
+    st = fn(srv, rid, C.byref(s))
+    if st != OK:
+        raise EssError(st, "unknown request")
+    return {k: getattr(s, k) for k, _ in RequestStatus._fields_}
+
+
+def ess_server_poll(srv, rid):
+    return _status(lib.ess_server_poll, srv, rid)
+
+
+def ess_server_wait(srv, rid):
+    return _status(lib.ess_server_wait, srv, rid)
+
+
+def ess_server_drain(srv):
+    if lib.ess_server_drain(srv) != OK:
+        raise EssError(ERR_ARG, "ess_server_drain failed")
+
+
+def ess_server_destroy(srv):
+    if lib.ess_server_destroy(srv) != OK:
+        raise EssError(ERR_ARG, "ess_server_destroy failed")
 
 
 def ess_launch_count(ctx):

@@ -155,3 +155,26 @@ def test_invalid_inputs_are_rejected(gpu, ctx):
         ess.ess_release(ctx, vol)                  # still used by st
     ess.ess_release(ctx, st)
     ess.ess_release(ctx, vol)
+
+
+@pytest.mark.parametrize("case", VOLS, ids=lambda c: c[0])
+def test_dense_and_cell_samplers_agree(gpu, ctx, ora, case):
+    """Dense voxel reads and the corner-replicated cell copy give the same
+    bits, and both match the oracle."""
+    ess, torch = gpu
+    name, v, (lo, hi), tf = case
+    vol, t = upload(ess, torch, ctx, v, lo, hi, tf)
+    ov, ot = ora.OVolume(v, lo, hi), ora.OTF(tf)
+    rng = np.random.default_rng(21)
+    sts = [ess.ess_build(ctx, vol, t, k, ess.build_params(brick=8)) for k in ess.KINDS]
+    for cam in (synth.random_camera(ov.dims, rng, ortho=False),
+                synth.random_camera(ov.dims, rng, ortho=True)):
+        ref, _ = ora.render_naive(ov, ot, cam, 45, 35, ert=0.97)
+        imgs = []
+        for cells in (1, 0, 1):
+            ess.ess_volume_set_sampler(ctx, vol, cells)
+            for st in sts:
+                imgs.append(render(ess, torch, ctx, st, cam, 45, 35, ert=0.97))
+        assert_image_parity(imgs[0], ref, name)
+        for im in imgs[1:]:
+            assert np.array_equal(bits(im), bits(imgs[0]))
