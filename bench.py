@@ -231,6 +231,221 @@ def run_reference(args, rank):
 METRIC = ("ray samples/s (naive-equivalent) over TF edit + rebuild + render of grid, "
           "LBVH and k-d structures")
 
+BATCH_SIZES = [(256, 256), (512, 512), (1024, 1024), (1920, 1080)]
+
+
+def run_batched(ess, torch, dev, stream, ctx, reps=3):
+    """512^3 uint16 volume x 64 random piecewise-linear TFs x 4 views with
+    image sizes drawn from 256^2 .. 1920x1080: autotuned structure kind, brick
+    and tile shape; 256 sequential ess_render calls against one
+    ess_render_batch launch (captured graph), same outputs."""
+    from paper_1912_09596_gb300 import synth
+    dims = (512, 512, 512)
+    v = synth.ct_like_u16(dims, seed=3)
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(v).to(dev), 0, 65535)
+    del v
+    tfs = [synth.tf_piecewise_random(1024, seed=500 + i) for i in range(64)]
+    tf_handles = [ess.ess_tf_set(ctx, torch.from_numpy(t).to(dev)) for t in tfs]
+    rng = np.random.default_rng(42)
+    views = [synth.orbit_camera(dims, 1024, 1024, theta=float(rng.uniform(0, 2 * math.pi)),
+                                phi=float(rng.uniform(-0.6, 0.6)), dist=1.7) for _ in range(4)]
+    rp = ess.render_params(0.5, 0.99)
+    best = ess.ess_autotune(ctx, vol, tf_handles[0], views[:2], rp, 1024, 1024, frames_per_edit=4.0)
+    kdp = dict(KD_PARAMS)
+    sts = [ess.ess_build(ctx, vol, t, best["kind"], ess.build_params(brick=best["brick"], **kdp))
+           for t in tf_handles]
+    items_plain, items_batch = [], []
+    for i in range(256):
+        W, H = BATCH_SIZES[int(rng.integers(len(BATCH_SIZES)))]
+        cam = synth.orbit_camera(dims, W, H, theta=2 * math.pi * (i % 4) / 4 + 0.3, phi=0.3, dist=1.7)
+        st = sts[i // 4]
+        items_plain.append((st, cam, W, H, torch.empty((H, W, 4), dtype=torch.float32, device=dev)))
+        items_batch.append((st, cam, rp, W, H, torch.empty((H, W, 4), dtype=torch.float32, device=dev)))
+    rpt = ess.render_params(0.5, 0.99, tile_w=best["tile_w"])
+    ecams = [ess.camera_from(it[1]) for it in items_plain]
+
+    def plain():
+        for (st, cam, W, H, out), ec in zip(items_plain, ecams):
+            ess.ess_render(ctx, st, ec, rpt, W, H, out)
+
+    def batched():
+        ess.ess_render_batch(ctx, items_batch, tile_w=best["tile_w"])
+
+    def timeit(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    t_plain = timeit(plain)
+    t_batch = timeit(batched)
+    same = all(torch.equal(a[4], b[5]) for a, b in zip(items_plain, items_batch))
+    pixels = sum(W * H for (_, _, W, H, _) in items_plain)
+    out = {"workload": "512^3 uint16 CT-like, 64 random piecewise-linear TFs (1024 entries) x 4 "
+                       "views, image sizes drawn from 256^2, 512^2, 1024^2, 1920x1080, dt 0.5, "
+                       "ERT 0.99",
+           "images": 256, "megapixels": round(pixels / 1e6, 2),
+           "autotune": {"kind": ess.KIND_NAMES[best["kind"]], "brick": best["brick"],
+                        "tile_w": best["tile_w"], "build_ms": round(best["build_ms"], 3),
+                        "render_ms_1024sq": round(best["render_ms"], 3)},
+           "plain_ms": round(t_plain, 3), "batched_ms": round(t_batch, 3),
+           "plain_frames_per_s": 256 / (t_plain / 1000.0),
+           "batched_frames_per_s": 256 / (t_batch / 1000.0),
+           "speedup": t_plain / t_batch, "bit_identical": bool(same)}
+    for st in sts:
+        ess.ess_release(ctx, st)
+    for t in tf_handles:
+        ess.ess_release(ctx, t)
+    ess.ess_release(ctx, vol)
+    return out
+
+
+SERVE_SIZES = [(256, 256), (512, 512), (1024, 768), (1920, 1080)]
+
+
+def serve_scene(ess, torch, dev, ctx, ct512):
+    """6 resident volumes from the workload generators, each with one
+    structure (kinds in turn) and its own TF."""
+    from paper_1912_09596_gb300 import synth
+    vols = [("128^3 u8 blobs", synth.blobs_u8((128, 128, 128), seed=0), 0, 255, 256),
+            ("256^3 u8 blobs", synth.blobs_u8((256, 256, 256), n_blobs=24, seed=5), 0, 255, 256),
+            ("512^3 u8 CT-like", ct512, 0, 255, 256),
+            ("256^3 f32 fractal", synth.fractal_f32((256, 256, 256), seed=2), 0.0, 1.0, 1024),
+            ("512^3 u16 CT-like", synth.ct_like_u16((512, 512, 512), seed=3), 0, 65535, 1024),
+            ("1024^3 f32 fractal", None, 0.0, 1.0, 1024)]
+    scene = []
+    kinds = [ess.GRID, ess.LBVH, ess.KD]
+    for i, (name, v, lo, hi, nt) in enumerate(vols):
+        if v is None:
+            data = synth.fractal_f32_torch((1024, 1024, 1024), seed=2, device=dev)
+            dims = (1024, 1024, 1024)
+        else:
+            data = torch.from_numpy(v).to(dev)
+            dims = v.shape[::-1]
+        vol = ess.ess_volume_upload(ctx, data, lo, hi)
+        del data
+        tf0 = synth.tf_piecewise_random(nt, seed=700 + i)
+        t = ess.ess_tf_set(ctx, torch.from_numpy(tf0).to(dev))
+        kind = kinds[i % 3]
+        st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=8, **KD_PARAMS))
+        scene.append(dict(name=name, vol=vol, tf=t, st=st, dims=dims, nt=nt, kind=kind, tf0=tf0))
+    torch.cuda.synchronize(dev)
+    return scene
+
+
+def serve_requests(ess, scene, n, seed):
+    from paper_1912_09596_gb300 import synth
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        j = int(rng.integers(len(scene)))
+        W, H = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
+        edit = rng.random() < 0.3
+        cam = synth.orbit_camera(scene[j]["dims"], W, H, theta=float(rng.uniform(0, 2 * math.pi)),
+                                 phi=float(rng.uniform(-0.6, 0.6)), dist=float(rng.uniform(1.4, 2.2)))
+        reqs.append(dict(scene=j, W=W, H=H, edit=edit, cam=ess.camera_from(cam),
+                         rgba=synth.tf_piecewise_random(scene[j]["nt"], seed=9000 + i) if edit else None))
+    return reqs
+
+
+def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
+    """Poisson stream of render and TF-edit requests (30 % edits) over 6
+    resident volumes, image sizes 256^2 .. 1920x1080.  Serial plain processing
+    (one request at a time through ess_render with a host image) against the
+    continuous-batching server, both fed at the same arrival times; the rate is
+    `load` times the serial service rate measured first."""
+    import threading
+    scene = serve_scene(ess, torch, dev, ctx, ct512)
+    reqs = serve_requests(ess, scene, n_req, seed=11)
+    outs = [torch.empty((r["H"], r["W"], 4), dtype=torch.float32).pin_memory() for r in reqs]
+    rp = ess.render_params(0.5, 0.99)
+
+    def serve_one(r, out):
+        sc = scene[r["scene"]]
+        if r["edit"]:
+            ess.ess_tf_update(ctx, sc["tf"], r["rgba"])
+            ess.ess_rebuild(ctx, sc["st"])
+        ess.ess_render(ctx, sc["st"], r["cam"], rp, r["W"], r["H"], out)
+
+    # serial service rate, back to back
+    for r, o in zip(reqs[:10], outs[:10]):
+        serve_one(r, o)
+    t0 = time.perf_counter()
+    for r, o in zip(reqs[:40], outs[:40]):
+        serve_one(r, o)
+    mu = 40 / (time.perf_counter() - t0)
+    lam = load * mu
+    gaps = np.random.default_rng(12).exponential(1.0 / lam, size=n_req)
+    arrivals = np.cumsum(gaps)
+
+    def reset():
+        for sc in scene:
+            ess.ess_tf_update(ctx, sc["tf"], sc["tf0"])
+            ess.ess_rebuild(ctx, sc["st"])
+        ess.ess_sync(ctx)
+
+    def run_serial():
+        reset()
+        lat = []
+        start = time.perf_counter()
+        for r, o, at in zip(reqs, outs, arrivals):
+            now = time.perf_counter() - start
+            if now < at:
+                time.sleep(at - now)
+            serve_one(r, o)
+            lat.append((time.perf_counter() - start - at) * 1000.0)
+        return lat, time.perf_counter() - start
+
+    lat_plain, span_plain = run_serial()
+    plain_imgs = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(-1.0)
+    reset()
+    srv = ess.ess_server_create(ctx, memory_budget=8 << 30, max_batch=64, max_inflight=2)
+    ids = [None] * n_req
+    start = time.perf_counter()
+
+    def producer():
+        for k, (r, o, at) in enumerate(zip(reqs, outs, arrivals)):
+            now = time.perf_counter() - start
+            if now < at:
+                time.sleep(at - now)
+            sc = scene[r["scene"]]
+            ids[k] = ess.ess_server_submit(srv, ess.REQ_EDIT if r["edit"] else ess.REQ_RENDER,
+                                           sc["st"], r["cam"], rp, r["W"], r["H"], o, rgba=r["rgba"])
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    ess.ess_server_drain(srv)
+    span_served = time.perf_counter() - start
+    st = [ess.ess_server_wait(srv, i) for i in ids]
+    ess.ess_server_destroy(srv)
+    lat_served = [s["latency_ms"] for s in st]
+    ok = all(s["status"] == ess.OK for s in st)
+    # the served images must equal the serial ones: both apply the same edits in order
+    same = all(torch.equal(a, b) for a, b in zip(plain_imgs, outs))
+    pct = lambda a, q: float(np.percentile(np.asarray(a), q))
+    return {
+        "workload": "6 resident volumes (" + ", ".join(s["name"] for s in scene) + "), kinds "
+                    "grid/lbvh/kd in turn, brick 8; Poisson arrivals, 30% TF edits (rebuild), "
+                    "image sizes 256^2..1920x1080, dt 0.5, ERT 0.99; images read back to pinned "
+                    "host memory",
+        "requests": n_req, "rate_hz": round(lam, 2), "serial_service_rate_hz": round(mu, 2),
+        "plain": {"frames_per_s": n_req / span_plain, "p50_ms": pct(lat_plain, 50),
+                  "p99_ms": pct(lat_plain, 99)},
+        "served": {"frames_per_s": n_req / span_served, "p50_ms": pct(lat_served, 50),
+                   "p99_ms": pct(lat_served, 99), "all_ok": ok},
+        "bit_identical_to_plain": bool(same),
+    }
+
 
 # ---------------------------------------------------------------- ours
 def run_ours(args, rank, local, ws, dist):
@@ -396,6 +611,12 @@ def run_ours(args, rank, local, ws, dist):
                 "ms_per_step": e2e_ms / args.steps},
         "clocks": clk,
     }
+    if not args.no_batched:
+        with torch.cuda.stream(stream):
+            result["batched"] = run_batched(ess, torch, dev, stream, ctx)
+    if not args.no_serve:
+        with torch.cuda.stream(stream):
+            result["served"] = run_served(ess, torch, dev, ctx, vol_np)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
         rate, desc = oracle_rate(vol_np, vlo, vhi, tfs_np[0], cams[0], w, args.ref_budget, cores)
@@ -417,6 +638,10 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=6.0,
                     help="seconds of oracle work per CPU measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-render comparison (64 TFs x 4 views)")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving comparison (Poisson request stream)")
     args = ap.parse_args()
     rank, local, ws, dist = dist_setup()
     if args.impl == "reference":

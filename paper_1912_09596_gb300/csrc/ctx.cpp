@@ -220,14 +220,9 @@ void free_structure(Ctx &c, Structure &s)
     void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_sorted, s.ids_sorted,
                     s.keys_alt, s.ids_alt, s.sort_scratch, s.left, s.right, s.parent,
                     s.leaf_parent, s.inner_box, s.arrive, s.nodes, s.root, s.kd_nodes,
-                    s.kd_count_dev, s.brick_node, s.kd_scratch_i32, s.kd_splits_dev};
+                    s.kd_count_dev, s.brick_node, s.kd_scratch_i32, s.kd_state};
     for (void *p : ptrs) c.free(p);
     kd_free(c, s);
-    if (s.kd_splits_host) {
-        cudaStreamSynchronize(c.stream);
-        cudaFreeHost(s.kd_splits_host);
-        s.kd_splits_host = nullptr;
-    }
 }
 
 template <typename P> P *alloc_n(Ctx &c, Structure &s, size_t n)
@@ -269,17 +264,7 @@ void alloc_kd(Ctx &c, Structure &s)
     s.kd_count_dev = alloc_n<int>(c, s, 1);
     s.brick_node = alloc_n<int>(c, s, cap);
     s.kd_scratch_i32 = alloc_n<int32_t>(c, s, 8);
-    s.kd_splits_dev = alloc_n<int>(c, s, 1);
-    ESS_CUDA(cudaMallocHost(&s.kd_splits_host, sizeof(int)));
-}
-
-int64_t nonempty_count_sync(Ctx &c, Structure &s)
-{
-    int n = 0;
-    ESS_CUDA(cudaMemcpyAsync(&n, s.count, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-    ESS_CUDA(cudaStreamSynchronize(c.stream));
-    s.n_host = n;
-    return n;
+    s.kd_state = alloc_n<int32_t>(c, s, 8);
 }
 
 // The empty test and compaction (Sec. 3.1), then the kind-specific build.
@@ -302,7 +287,7 @@ void run_build(Ctx &c, Structure &s)
     if (s.kind == ESS_LBVH) launch_lbvh(c, s);
     if (s.kind == ESS_KD) {
         s.volume = &v;
-        launch_kd(c, s, nonempty_count_sync(c, s));
+        launch_kd(c, s);
     }
     s.tf_version = t.version;
 }
@@ -647,6 +632,7 @@ ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_struct
             info->height = s.height;
         }
         if (s.kind == ESS_KD) {
+            kd_stats(c, s);
             info->n_nodes = s.kd_count;
             info->height = s.height;
         }
@@ -693,6 +679,7 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
         }
         case ESS_ARR_KD_NODES:
             ESS_REQUIRE(s.kind == ESS_KD, "array only exists for a k-d tree");
+            kd_stats(c, s);
             copy_out(c, dst, s.kd_nodes, sizeof(int32_t) * 9 * (size_t)s.kd_count, capacity, written);
             break;
         default: throw Error{ESS_ERR_ARG, "array not available for this structure kind"};

@@ -125,8 +125,9 @@ struct Structure {
     size_t kd_dec_cap = 0;
     uint32_t *kd_block_sums = nullptr;
     size_t kd_bs_cap = 0;
-    int *kd_splits_dev = nullptr;
-    int *kd_splits_host = nullptr;              // pinned
+    void *kd_state = nullptr;                   // device level state (32 bytes)
+    cudaGraph_t kd_graph = nullptr;             // device-driven build (binned planes)
+    cudaGraphExec_t kd_exec = nullptr;
     size_t device_bytes = 0;
     bool released = false;
 };
@@ -211,7 +212,8 @@ void launch_lbvh(Ctx &c, Structure &s);
 int lbvh_height(Ctx &c, Structure &s);
 
 // kd.cu
-void launch_kd(Ctx &c, Structure &s, int64_t n);
+void launch_kd(Ctx &c, Structure &s);
+void kd_stats(Ctx &c, Structure &s);
 void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur);
 void kd_free(Ctx &c, Structure &s);
 

@@ -108,7 +108,41 @@ __device__ __forceinline__ void slab_reset(int32_t *slot)
     slot[3] = slot[4] = slot[5] = INT_MIN;
 }
 
+// Level state, in device memory so that the level loop can run without the
+// host: the kernels of a level read it, the advance kernel moves it on.
+struct KdState {
+    int prev_begin;  // first node of the previous level
+    int lvl_begin;   // first node of the current level
+    int lvl_size;    // nodes on the current level (0: done)
+    int levels;      // levels started so far; the current level is number `levels`
+    int splits;      // splits on the current level (from the scan)
+    int pad[3];
+};
+
+// Slab buffer of the current level (parity of the level number) and of the next.
+__device__ __forceinline__ int32_t *kd_cur_slabs(int32_t *s0, int32_t *s1, const KdState *st)
+{
+    return (st->levels & 1) ? s1 : s0;
+}
+__device__ __forceinline__ int32_t *kd_next_slabs(int32_t *s0, int32_t *s1, const KdState *st)
+{
+    return (st->levels & 1) ? s0 : s1;
+}
+
 // -------------------------------------------------------------- root box
+__global__ void k_kd_root_init(int32_t *root_box, KdState *st)
+{
+    if (threadIdx.x == 0) {
+        root_box[0] = root_box[1] = root_box[2] = INT_MAX;
+        root_box[3] = root_box[4] = root_box[5] = INT_MIN;
+        st->prev_begin = 0;
+        st->lvl_begin = 0;
+        st->lvl_size = 1;
+        st->levels = 0;
+        st->splits = 0;
+    }
+}
+
 __global__ void k_kd_root_reduce(const uint32_t *__restrict__ ids, const int *__restrict__ count,
                                  int gx, int gy, int32_t *root_box)
 {
@@ -136,18 +170,22 @@ __global__ void k_kd_root_reduce(const uint32_t *__restrict__ ids, const int *__
     }
 }
 
-// node 0 record and the slabs of level 0
-__global__ void k_kd_init(const int32_t *__restrict__ root_box, int32_t *nodes9, int32_t *slabs,
-                          int S)
+// node 0 record and the slabs of level 0 (no level at all for an empty mask)
+__global__ void k_kd_init(const int *__restrict__ count, const int32_t *__restrict__ root_box,
+                          int32_t *nodes9, int32_t *slabs0, int S, KdState *st)
 {
     int t = threadIdx.x;
+    if (*count <= 0) {
+        if (t == 0) st->lvl_size = 0;
+        return;
+    }
     if (t < 6) nodes9[t] = root_box[t];
     if (t == 0) {
         nodes9[6] = -1;
         nodes9[7] = 0;
         nodes9[8] = -1;
     }
-    for (int s = t; s < 3 * S; s += blockDim.x) slab_reset(slabs + 6 * s);
+    for (int s = t; s < 3 * S; s += blockDim.x) slab_reset(slabs0 + 6 * s);
 }
 
 // ------------------------------------------------------------ per level
@@ -156,39 +194,65 @@ __global__ void k_kd_init(const int32_t *__restrict__ root_box, int32_t *nodes9,
 // current level.
 __global__ void k_kd_accumulate(const uint32_t *__restrict__ ids, const int *__restrict__ count,
                                 int *__restrict__ brick_node, const int32_t *__restrict__ nodes9,
-                                int prev_begin, int lvl_begin, int lvl_size, int32_t *slabs,
-                                KdParams P)
+                                int32_t *slabs0, int32_t *slabs1, const KdState *st, KdParams P)
 {
+    const int prev_begin = st->prev_begin, lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if (lvl_size <= 0) return;
+    int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
     int n = *count;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c[3];
-    brick_coords(ids[i], P.gx, P.gy, c);
-    int node = lvl_begin == 0 ? 0 : brick_node[i];
-    if (node >= prev_begin && node < lvl_begin) {
-        const int32_t *rec = nodes9 + 9 * (size_t)node;
-        int fc = rec[8];
-        if (fc >= 0) {
-            node = fc + (c[rec[6]] >= rec[7] ? 1 : 0);
-            brick_node[i] = node;
+    bool live = i < n;
+    int c[3] = {0, 0, 0};
+    int node = -1;
+    if (live) {
+        brick_coords(ids[i], P.gx, P.gy, c);
+        node = lvl_begin == 0 ? 0 : brick_node[i];
+        if (node >= prev_begin && node < lvl_begin) {
+            const int32_t *rec = nodes9 + 9 * (size_t)node;
+            int fc = rec[8];
+            if (fc >= 0) {
+                node = fc + (c[rec[6]] >= rec[7] ? 1 : 0);
+                brick_node[i] = node;
+            }
+        } else if (lvl_begin == 0) {
+            brick_node[i] = 0;
         }
-    } else if (lvl_begin == 0) {
-        brick_node[i] = 0;
+        if (node < lvl_begin || node >= lvl_begin + lvl_size) live = false;
     }
-    if (node < lvl_begin || node >= lvl_begin + lvl_size) return;
-    const int32_t *box = nodes9 + 9 * (size_t)node;
+    const int32_t *box = nodes9 + 9 * (size_t)(live ? node : 0);
     int local = node - lvl_begin;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (box[3 + a] - box[a] < 2) continue;
-        int s = kd_slab_of(c[a], box[a], box[3 + a], P.nbins);
-        int32_t *slot = slabs + 6 * (((size_t)local * 3 + a) * P.S + s);
-        atomicMin(slot + 0, c[0]);
-        atomicMin(slot + 1, c[1]);
-        atomicMin(slot + 2, c[2]);
-        atomicMax(slot + 3, c[0] + 1);
-        atomicMax(slot + 4, c[1] + 1);
-        atomicMax(slot + 5, c[2] + 1);
+        bool use = live && box[3 + a] - box[a] >= 2;
+        int s = use ? kd_slab_of(c[a], box[a], box[3 + a], P.nbins) : 0;
+        long long slot_id = use ? ((long long)local * 3 + a) * P.S + s : -1;
+        // near the root whole warps update the same slab: reduce in the warp
+        // and let one lane do the atomics (min/max are order independent)
+        long long first = __shfl_sync(0xffffffffu, slot_id, 0);
+        if (__all_sync(0xffffffffu, slot_id == first)) {
+            if (first < 0) continue;
+            int v[6] = {c[0], c[1], c[2], c[0] + 1, c[1] + 1, c[2] + 1};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                v[k] = __reduce_min_sync(0xffffffffu, v[k]);
+                v[3 + k] = __reduce_max_sync(0xffffffffu, v[3 + k]);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                int32_t *slot = slabs + 6 * first;
+                for (int k = 0; k < 3; ++k) {
+                    atomicMin(slot + k, v[k]);
+                    atomicMax(slot + 3 + k, v[3 + k]);
+                }
+            }
+        } else if (use) {
+            int32_t *slot = slabs + 6 * slot_id;
+            atomicMin(slot + 0, c[0]);
+            atomicMin(slot + 1, c[1]);
+            atomicMin(slot + 2, c[2]);
+            atomicMax(slot + 3, c[0] + 1);
+            atomicMax(slot + 4, c[1] + 1);
+            atomicMax(slot + 5, c[2] + 1);
+        }
     }
 }
 
@@ -205,11 +269,14 @@ __device__ __forceinline__ void box_union(int32_t *acc, const int32_t *s)
 // suffix unions of the slab boxes, then the split rule.  `vr` is scratch for
 // suffix volumes.  Writes the decision and the block's split count.
 __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ nodes9,
-                                                   int lvl_begin, int lvl_size,
-                                                   const int32_t *__restrict__ slabs,
+                                                   int32_t *slabs0, int32_t *slabs1,
                                                    unsigned long long *vr, KdDecision *dec,
-                                                   uint32_t *block_sums, KdParams P)
+                                                   uint32_t *block_sums, const KdState *st,
+                                                   KdParams P)
 {
+    const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if ((int)(blockIdx.x * blockDim.x) >= lvl_size) return;  // uniform per block
+    const int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     int split = 0;
     if (l < lvl_size) {
@@ -292,11 +359,12 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
     if (threadIdx.x == 0) block_sums[blockIdx.x] = (uint32_t)total;
 }
 
-// exclusive scan of the block split counts; total splits -> *splits
-__global__ void __launch_bounds__(1024) k_kd_scan(uint32_t *block_sums, int nblk, int *splits)
+// exclusive scan of the level's block split counts; total -> st->splits
+__global__ void __launch_bounds__(1024) k_kd_scan(uint32_t *block_sums, KdState *st)
 {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
+    const int nblk = (st->lvl_size + 255) / 256;
     int t = threadIdx.x, lane = t & 31, w = t >> 5;
     if (t == 0) carry = 0;
     __syncthreads();
@@ -327,18 +395,21 @@ __global__ void __launch_bounds__(1024) k_kd_scan(uint32_t *block_sums, int nblk
         if (t == 0) carry += wsum[31];
         __syncthreads();
     }
-    if (t == 0) *splits = (int)carry;
+    if (t == 0) st->splits = (int)carry;
 }
 
 // Writes split decisions into the node records, creates the children (BFS
 // numbering: after all nodes of this level, in node order, left first) and
 // resets their slabs for the next level.
-__global__ void __launch_bounds__(256) k_kd_emit(int lvl_begin, int lvl_size,
-                                                 const KdDecision *__restrict__ dec,
+__global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ dec,
                                                  const uint32_t *__restrict__ block_off,
-                                                 int32_t *nodes9, int32_t *next_slabs, int S,
-                                                 int capacity, uint32_t *status)
+                                                 int32_t *nodes9, int32_t *slabs0, int32_t *slabs1,
+                                                 int S, int capacity, uint32_t *status,
+                                                 const KdState *st)
 {
+    const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if ((int)(blockIdx.x * blockDim.x) >= lvl_size) return;  // uniform per block
+    int32_t *next_slabs = kd_next_slabs(slabs0, slabs1, st);
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     int split = l < lvl_size ? dec[l].split : 0;
     // block-local exclusive rank of the split flag
@@ -377,13 +448,37 @@ __global__ void __launch_bounds__(256) k_kd_emit(int lvl_begin, int lvl_size,
     }
 }
 
+// Moves the level state on; in the graph build it also decides on the device
+// whether the level loop continues.  A tree that would exceed the node
+// capacity or the renderer's depth limit stops with DEV_ERR_OVERFLOW.
+__global__ void k_kd_advance(KdState *st, int capacity, int max_levels, uint32_t *status,
+                             cudaGraphConditionalHandle handle, int use_handle)
+{
+    if (threadIdx.x != 0) return;
+    int size = st->lvl_size;
+    if (size > 0) {
+        int next = 2 * st->splits;
+        st->prev_begin = st->lvl_begin;
+        st->lvl_begin += size;
+        st->levels += 1;
+        if (next > 0 && (st->lvl_begin + next > capacity || st->levels >= max_levels)) {
+            atomicOr(status, DEV_ERR_OVERFLOW);
+            next = 0;
+        }
+        st->lvl_size = next;
+        st->splits = 0;
+    }
+    if (use_handle) cudaGraphSetConditional(handle, st->lvl_size > 0 ? 1u : 0u);
+}
+
 // Traversal layout: one BoxNode per node id (leaf entries unused), children
-// referenced as node ids, leaves as -1 - id; the root record.
-__global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const int *__restrict__ m_dev,
+// referenced as node ids, leaves as -1 - id; the root record and node count.
+__global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const KdState *st, int *m_dev,
                           BoxNode *nodes, int32_t *root)
 {
-    int m = *m_dev;
+    int m = st->lvl_begin;  // all levels done: every node id is below this
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *m_dev = m;
     if (i >= m) return;
     const int32_t *rec = nodes9 + 9 * (size_t)i;
     if (i == 0) {
@@ -404,30 +499,55 @@ __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const int *__restr
 }
 
 // ------------------------------------------------------------------ host
-// Per-level buffers: the current level's slabs were reset by the previous
-// level's emit and already fit; the next level (at most twice as many nodes)
-// may need a larger buffer, whose old contents are not needed.
+static int kd_slots(const Structure &s)
+{
+    if (s.p.nbins != 0) return s.p.nbins;
+    return std::max(s.gx, std::max(s.gy, s.gz));
+}
+
+static KdParams kd_params(const Structure &s)
+{
+    KdParams P;
+    const Volume *v = s.volume;
+    P.B = s.p.brick;
+    P.nx = v->nx;
+    P.ny = v->ny;
+    P.nz = v->nz;
+    P.gx = s.gx;
+    P.gy = s.gy;
+    P.nbins = s.p.nbins;
+    P.halting = s.p.halting;
+    P.mls3 = s.p.mls > 0 ? (unsigned long long)s.p.mls * s.p.mls * s.p.mls : 0ull;
+    P.S = kd_slots(s);
+    return P;
+}
+
+static void grow(Ctx &c, void *&p, size_t &cap, size_t need, size_t elem)
+{
+    if (cap >= need) return;
+    c.free(p);
+    size_t n = std::max(need, cap * 2);
+    p = c.alloc(n * elem);
+    cap = n;
+}
+
+// Per-level buffers of the host loop: the current level's slabs were reset
+// by the previous level's emit and already fit; the next level (at most twice
+// as many nodes) may need a larger buffer, whose old contents are not needed.
 void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur)
 {
     size_t slab_words = (size_t)3 * S * 6;
-    auto grow = [&](void *&p, size_t &cap, size_t need, size_t elem) {
-        if (cap >= need) return;
-        c.free(p);
-        size_t n = std::max(need, cap * 2);
-        p = c.alloc(n * elem);
-        cap = n;
-    };
     if (s.kd_slab_cap[cur] < (size_t)lvl_size)
         throw Error{ESS_ERR_ARG, "internal: k-d slab buffer of the current level too small"};
     void *nx = s.kd_slabs[cur ^ 1];
-    grow(nx, s.kd_slab_cap[cur ^ 1], (size_t)2 * lvl_size, slab_words * sizeof(int32_t));
+    grow(c, nx, s.kd_slab_cap[cur ^ 1], (size_t)2 * lvl_size, slab_words * sizeof(int32_t));
     s.kd_slabs[cur ^ 1] = (int32_t *)nx;
     void *vr = s.kd_vr;
-    grow(vr, s.kd_vr_cap, (size_t)lvl_size * 3 * S, sizeof(unsigned long long));
+    grow(c, vr, s.kd_vr_cap, (size_t)lvl_size * 3 * S, sizeof(unsigned long long));
     s.kd_vr = (unsigned long long *)vr;
-    grow(s.kd_dec, s.kd_dec_cap, (size_t)lvl_size, sizeof(KdDecision));
+    grow(c, s.kd_dec, s.kd_dec_cap, (size_t)lvl_size, sizeof(KdDecision));
     void *bs = s.kd_block_sums;
-    grow(bs, s.kd_bs_cap, (size_t)(lvl_size + 255) / 256, sizeof(uint32_t));
+    grow(c, bs, s.kd_bs_cap, (size_t)(lvl_size + 255) / 256, sizeof(uint32_t));
     s.kd_block_sums = (uint32_t *)bs;
 }
 
@@ -440,108 +560,185 @@ void kd_free(Ctx &c, Structure &s)
     s.kd_dec = nullptr;
     s.kd_block_sums = nullptr;
     s.kd_slab_cap[0] = s.kd_slab_cap[1] = s.kd_vr_cap = s.kd_dec_cap = s.kd_bs_cap = 0;
+    if (s.kd_exec) cudaGraphExecDestroy(s.kd_exec);
+    if (s.kd_graph) cudaGraphDestroy(s.kd_graph);
+    s.kd_exec = nullptr;
+    s.kd_graph = nullptr;
 }
 
-static int kd_slots(const Structure &s)
+// The root part of a build: root box, node 0, level-0 slabs.
+static void kd_root_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks)
 {
-    if (s.p.nbins != 0) return s.p.nbins;
-    return std::max(s.gx, std::max(s.gy, s.gz));
+    KdState *st = (KdState *)s.kd_state;
+    k_kd_root_init<<<1, 32, 0, c.stream>>>(s.kd_scratch_i32, st);
+    k_kd_root_reduce<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.gx, s.gy,
+                                                         s.kd_scratch_i32);
+    k_kd_init<<<1, 256, 0, c.stream>>>(s.count, s.kd_scratch_i32, s.kd_nodes, s.kd_slabs[0], P.S,
+                                       st);
 }
 
-void launch_kd(Ctx &c, Structure &s, int64_t n)
+// One level: accumulate, decide, scan, emit, advance.
+static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks,
+                              unsigned node_blocks, cudaGraphConditionalHandle h, int use_handle)
 {
-    KdParams P;
-    Volume *v = s.volume;
-    P.B = s.p.brick;
-    P.nx = v->nx;
-    P.ny = v->ny;
-    P.nz = v->nz;
-    P.gx = s.gx;
-    P.gy = s.gy;
-    P.nbins = s.p.nbins;
-    P.halting = s.p.halting;
-    P.mls3 = s.p.mls > 0 ? (unsigned long long)s.p.mls * s.p.mls * s.p.mls : 0ull;
-    P.S = kd_slots(s);
-    s.height = 0;
-    s.kd_count = 0;
-    if (n <= 0) {
-        ESS_CUDA(cudaMemsetAsync(s.kd_count_dev, 0, sizeof(int), c.stream));
+    KdState *st = (KdState *)s.kd_state;
+    k_kd_accumulate<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node, s.kd_nodes,
+                                                        s.kd_slabs[0], s.kd_slabs[1], st, P);
+    k_kd_decide<<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], s.kd_vr,
+                                                   (KdDecision *)s.kd_dec, s.kd_block_sums, st, P);
+    k_kd_scan<<<1, 1024, 0, c.stream>>>(s.kd_block_sums, st);
+    k_kd_emit<<<node_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
+                                                 s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], P.S,
+                                                 s.kd_capacity, c.dev_status, st);
+    k_kd_advance<<<1, 32, 0, c.stream>>>(st, s.kd_capacity, KD_MAX_LEVELS, c.dev_status, h,
+                                         use_handle);
+}
+
+// Whether the whole build runs as one device-driven graph: binned planes and
+// level buffers for the widest possible level (one node per non-empty brick)
+// within an eighth of the free memory.
+static bool kd_graph_fits(const Structure &s, int S)
+{
+    if (s.p.nbins == 0) return false;
+    size_t cap = (size_t)s.nb;
+    size_t bytes = 2 * cap * 3 * S * 6 * sizeof(int32_t) + cap * 3 * S * sizeof(unsigned long long) +
+                   cap * sizeof(KdDecision) + ((cap + 255) / 256) * sizeof(uint32_t);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+    return bytes < free_b / 8;
+}
+
+static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
+{
+    size_t cap = (size_t)s.nb;
+    size_t slab_words = (size_t)3 * P.S * 6;
+    for (int b = 0; b < 2; ++b) {
+        void *p = s.kd_slabs[b];
+        grow(c, p, s.kd_slab_cap[b], std::max<size_t>(cap, 16), slab_words * sizeof(int32_t));
+        s.kd_slabs[b] = (int32_t *)p;
+    }
+    void *vr = s.kd_vr;
+    grow(c, vr, s.kd_vr_cap, cap * 3 * P.S, sizeof(unsigned long long));
+    s.kd_vr = (unsigned long long *)vr;
+    grow(c, s.kd_dec, s.kd_dec_cap, cap, sizeof(KdDecision));
+    void *bs = s.kd_block_sums;
+    grow(c, bs, s.kd_bs_cap, (cap + 255) / 256, sizeof(uint32_t));
+    s.kd_block_sums = (uint32_t *)bs;
+    if (!c.capture_stream)
+        ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
+
+    const unsigned brick_blocks = (unsigned)((cap + 255) / 256);
+    const unsigned node_blocks = brick_blocks;
+    cudaGraph_t g;
+    ESS_CUDA(cudaGraphCreate(&g, 0));
+    cudaStream_t saved = c.stream;
+    c.stream = c.capture_stream;
+    try {
+        // root part
+        ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, g, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        kd_root_launches(c, s, P, brick_blocks);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        ESS_CUDA(cudaStreamGetCaptureInfo(c.stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps));
+        std::vector<cudaGraphNode_t> tail(deps, deps + ndeps);
+        ESS_CUDA(cudaStreamEndCapture(c.stream, &g));
+        // level loop as a conditional while node
+        cudaGraphConditionalHandle h;
+        ESS_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t loop;
+        ESS_CUDA(cudaGraphAddNode(&loop, g, tail.data(), nullptr, tail.size(), &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        kd_level_launches(c, s, P, brick_blocks, node_blocks, h, 1);
+        ESS_CUDA(cudaStreamEndCapture(c.stream, &body));
+        // traversal layout after the loop
+        ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, g, &loop, nullptr, 1,
+                                               cudaStreamCaptureModeThreadLocal));
+        k_kd_pack<<<(unsigned)((2 * cap + 255) / 256), 256, 0, c.stream>>>(
+            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root);
+        ESS_CUDA(cudaStreamEndCapture(c.stream, &g));
+        ESS_CUDA(cudaGraphInstantiate(&s.kd_exec, g, 0));
+    } catch (...) {
+        c.stream = saved;
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(c.capture_stream, &cs) == cudaSuccess &&
+            cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(c.capture_stream, &tmp);
+            if (tmp && tmp != g) cudaGraphDestroy(tmp);
+        }
+        cudaGraphDestroy(g);
+        throw;
+    }
+    c.stream = saved;
+    s.kd_graph = g;
+}
+
+void launch_kd(Ctx &c, Structure &s)
+{
+    KdParams P = kd_params(s);
+    s.height = -1;
+    s.kd_count = -1;
+    if (s.kd_exec || kd_graph_fits(s, P.S)) {
+        // device-driven: the whole level loop is one graph launch
+        if (!s.kd_exec) kd_build_graph(c, s, P);
+        Launch L(c, "kd_build_graph");
+        ESS_CUDA(cudaGraphLaunch(s.kd_exec, c.stream));
         return;
     }
-    const int capacity = s.kd_capacity;
-    const unsigned bricks_blocks = (unsigned)((n + 255) / 256);
-    // root
-    int32_t init[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-    int32_t *root_box = s.kd_scratch_i32;
-    ESS_CUDA(cudaMemcpyAsync(root_box, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
-    {
-        Launch L(c, "kd_root");
-        k_kd_root_reduce<<<bricks_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.gx, s.gy,
-                                                              root_box);
-    }
-    if (s.kd_slab_cap[0] < 1) {
+    // host-driven level loop (exhaustive planes or buffers too large)
+    int64_t n_cap = s.nb;
+    const unsigned brick_blocks = (unsigned)((n_cap + 255) / 256);
+    if (s.kd_slab_cap[0] < 16) {
         c.free(s.kd_slabs[0]);
         s.kd_slabs[0] = (int32_t *)c.alloc(sizeof(int32_t) * 3 * P.S * 6 * 16);
         s.kd_slab_cap[0] = 16;
     }
     {
-        Launch L(c, "kd_init");
-        k_kd_init<<<1, 256, 0, c.stream>>>(root_box, s.kd_nodes, s.kd_slabs[0], P.S);
+        Launch L(c, "kd_root");
+        kd_root_launches(c, s, P, brick_blocks);
     }
-    int prev_begin = 0, lvl_begin = 0, lvl_size = 1, cur = 0;
-    int levels = 0;
-    while (lvl_size > 0) {
-        ++levels;
-        if (levels > KD_MAX_LEVELS)
-            throw Error{ESS_ERR_ARG, "k-d tree deeper than " + std::to_string(KD_MAX_LEVELS) +
-                                         " levels (renderer stack limit)"};
-        kd_reserve(c, s, lvl_size, P.S, cur);  // slabs for this level and 2x for the next
+    KdState hs{};
+    int lvl_size = 1, levels = 0;
+    while (true) {
+        int cur = levels & 1;
+        kd_reserve(c, s, lvl_size, P.S, cur);
         unsigned nblk = (unsigned)((lvl_size + 255) / 256);
         {
-            Launch L(c, "kd_accumulate");
-            k_kd_accumulate<<<bricks_blocks, 256, 0, c.stream>>>(
-                s.ids, s.count, s.brick_node, s.kd_nodes, prev_begin, lvl_begin, lvl_size,
-                s.kd_slabs[cur], P);
+            Launch L(c, "kd_level");
+            kd_level_launches(c, s, P, brick_blocks, nblk, 0, 0);
         }
-        {
-            Launch L(c, "kd_decide");
-            k_kd_decide<<<nblk, 256, 0, c.stream>>>(s.kd_nodes, lvl_begin, lvl_size,
-                                                    s.kd_slabs[cur], s.kd_vr,
-                                                    (KdDecision *)s.kd_dec, s.kd_block_sums, P);
-        }
-        {
-            Launch L(c, "kd_scan");
-            k_kd_scan<<<1, 1024, 0, c.stream>>>(s.kd_block_sums, (int)nblk, s.kd_splits_dev);
-        }
-        {
-            Launch L(c, "kd_emit");
-            k_kd_emit<<<nblk, 256, 0, c.stream>>>(lvl_begin, lvl_size, (const KdDecision *)s.kd_dec,
-                                                  s.kd_block_sums, s.kd_nodes, s.kd_slabs[cur ^ 1],
-                                                  P.S, capacity, c.dev_status);
-        }
-        ESS_CUDA(cudaMemcpyAsync(s.kd_splits_host, s.kd_splits_dev, sizeof(int),
-                                 cudaMemcpyDeviceToHost, c.stream));
+        ESS_CUDA(cudaMemcpyAsync(&hs, s.kd_state, sizeof(KdState), cudaMemcpyDeviceToHost,
+                                 c.stream));
         ESS_CUDA(cudaStreamSynchronize(c.stream));
-        int splits = *s.kd_splits_host;
-        prev_begin = lvl_begin;
-        lvl_begin += lvl_size;
-        lvl_size = 2 * splits;
-        if (lvl_begin + lvl_size > capacity) {
-            ESS_CUDA(cudaMemsetAsync(s.kd_count_dev, 0, sizeof(int), c.stream));
-            throw Error{ESS_ERR_ARG, "k-d node capacity exceeded"};
-        }
-        cur ^= 1;
+        lvl_size = hs.lvl_size;
+        levels = hs.levels;
+        if (lvl_size <= 0) break;
     }
-    s.kd_count = lvl_begin;
-    s.height = levels;
-    s.kd_count_i32 = (int)s.kd_count;
-    ESS_CUDA(cudaMemcpyAsync(s.kd_count_dev, &s.kd_count_i32, sizeof(int), cudaMemcpyHostToDevice,
-                             c.stream));
     {
         Launch L(c, "kd_pack");
-        k_kd_pack<<<(unsigned)((s.kd_count + 255) / 256), 256, 0, c.stream>>>(
-            s.kd_nodes, s.kd_count_dev, s.nodes, s.root);
+        k_kd_pack<<<(unsigned)((hs.lvl_begin + 255) / 256 + 1), 256, 0, c.stream>>>(
+            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root);
     }
+}
+
+// Node count and height of the last build (waits for it).
+void kd_stats(Ctx &c, Structure &s)
+{
+    if (s.kd_count >= 0) return;
+    KdState hs{};
+    ESS_CUDA(cudaMemcpyAsync(&hs, s.kd_state, sizeof(KdState), cudaMemcpyDeviceToHost, c.stream));
+    ESS_CUDA(cudaStreamSynchronize(c.stream));
+    s.kd_count = hs.lvl_begin;
+    s.height = hs.levels;
 }
 
 size_t kd_decision_bytes() { return sizeof(KdDecision); }

@@ -11,10 +11,12 @@
 // of the images to the callers' host buffers and records an event.  Up to
 // max_inflight batches are on the GPU at once; while they run, newly arrived
 // requests form the next batch, so requests are admitted as memory and slots
-// free up.  All GPU work stays on the context stream, so a rebuild can never
-// overtake a render of the same structure issued before it; within a batch a
-// request is not admitted if an edit in the batch would change the TF a
-// render already in the batch has to see (the batch is cut there).
+// free up.  Rebuilds and renders stay on the context stream, so a rebuild can
+// never overtake a render of the same structure issued before it; the image
+// copies of a batch run on a separate copy stream after that batch's render,
+// overlapping the next batch.  Within a batch a request is not admitted if an
+// edit in the batch would change the TF a render already in the batch has to
+// see (the batch is cut there).
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -65,6 +67,7 @@ struct ess_server {
     size_t in_use = 0;
     std::deque<Inflight> inflight;
     std::vector<cudaEvent_t> free_events;
+    cudaStream_t copy_stream = nullptr;  // image copies overlap the next batch
     std::string error;
 };
 
@@ -94,8 +97,7 @@ bool retire(ess_server *s, bool block)
         {
             std::lock_guard<std::mutex> lk(s->mtx);
             for (Req *q : f.reqs) {
-                if (q->dev_out) cudaFreeAsync(q->dev_out, s->ctx->c.stream);
-                q->dev_out = nullptr;
+                q->dev_out = nullptr;  // freed on the copy stream after its copy
                 finish_request(s, q, st);
             }
             s->in_use -= f.bytes;
@@ -192,18 +194,32 @@ void issue(ess_server *s, std::vector<Req *> &batch)
             ok.clear();
         }
     }
-    for (Req *q : ok)
-        cudaMemcpyAsync(q->r.out, q->dev_out, q->out_bytes, cudaMemcpyDeviceToHost, c.stream);
+    auto take_event = [&]() {
+        cudaEvent_t e;
+        if (!s->free_events.empty()) {
+            e = s->free_events.back();
+            s->free_events.pop_back();
+        } else {
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        }
+        return e;
+    };
+    // the copies wait for the batch's render on the copy stream, so the next
+    // batch can start on the context stream while they run
+    cudaEvent_t rendered = take_event();
+    cudaEventRecord(rendered, c.stream);
+    cudaStreamWaitEvent(s->copy_stream, rendered, 0);
+    for (Req *q : ok) {
+        cudaMemcpyAsync(q->r.out, q->dev_out, q->out_bytes, cudaMemcpyDeviceToHost,
+                        s->copy_stream);
+        cudaFreeAsync(q->dev_out, s->copy_stream);
+    }
     Inflight f;
     f.reqs = ok;
     f.bytes = bytes;
-    if (!s->free_events.empty()) {
-        f.ev = s->free_events.back();
-        s->free_events.pop_back();
-    } else {
-        cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming);
-    }
-    cudaEventRecord(f.ev, c.stream);
+    f.ev = take_event();
+    cudaEventRecord(f.ev, s->copy_stream);
+    s->free_events.push_back(rendered);  // reusable once recorded again later
     s->inflight.push_back(f);
     s->cv_done.notify_all();
 }
@@ -254,6 +270,10 @@ ess_status ess_server_create(ess_ctx *ctx, const ess_server_config *cfg, ess_ser
     if (!s) return ESS_ERR_OOM;
     s->ctx = ctx;
     s->cfg = c;
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return ESS_ERR_CUDA;
+    }
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return ESS_OK;
@@ -334,7 +354,9 @@ ess_status ess_server_destroy(ess_server *s)
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->copy_stream);
     for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+    cudaStreamDestroy(s->copy_stream);
     delete s;
     return ESS_OK;
 }

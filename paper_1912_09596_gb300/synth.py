@@ -165,6 +165,36 @@ def fractal_f32(dims=(1024, 1024, 1024), seed=2, octaves=4, threshold=0.42,
     return acc.astype(np.float32)
 
 
+def fractal_f32_torch(dims=(1024, 1024, 1024), seed=2, octaves=4, threshold=0.42,
+                      base_cells=8, device="cuda"):
+    """The fractal_f32 field computed with torch on `device` (for sizes that
+    numpy makes slowly): the same seeded lattices and fade matrices; float32
+    matrix products, so values may differ from fractal_f32 in low bits.
+    Returns a contiguous (nz, ny, nx) float32 tensor."""
+    import torch
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    acc = torch.zeros((nz, ny, nx), dtype=torch.float32, device=device)
+    amp, total = 1.0, 0.0
+    for o in range(octaves):
+        c = base_cells * (2 ** o)
+        lat = torch.from_numpy(rng.uniform(-1.0, 1.0, size=(c + 1, c + 1, c + 1))).to(device)
+        mx = torch.from_numpy(_fade_matrix(nx, c)).to(device)
+        my = torch.from_numpy(_fade_matrix(ny, c)).to(device)
+        mz = torch.from_numpy(_fade_matrix(nz, c)).to(device)
+        a = torch.einsum("zyc,xc->zyx", lat, mx)
+        a = torch.einsum("zcx,yc->zyx", a, my).float().reshape(c + 1, ny * nx)
+        mzf = mz.float()
+        for z0 in range(0, nz, 128):
+            z1 = min(nz, z0 + 128)
+            acc[z0:z1] += amp * (mzf[z0:z1] @ a).reshape(z1 - z0, ny, nx)
+        total += amp
+        amp *= 0.5
+    acc *= 1.0 / total
+    acc = ((acc - threshold) / (1.0 - threshold)).clamp_(0.0, 1.0)
+    return acc.contiguous()
+
+
 def ct_like_u16(dims=(512, 512, 512), seed=3) -> np.ndarray:
     """uint16 variant of the CT-like volume (values scaled by 257 plus a
     low-order smooth noise so that all 16 bits are in use)."""
