@@ -600,6 +600,8 @@ def run_ours(args, rank, local, ws, dist):
                    "l2": "flushed between timed steps (%d MiB write, untimed)" % (L2_FLUSH_BYTES >> 20),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "evaluated_samples_per_s": ws * evaluated_step * args.steps / (t_ms / 1000.0),
+        "samples_per_frame": {"naive_equivalent": float(np.mean(n_naive)),
+                              **{ess.KIND_NAMES[k]: float(np.mean(v)) for k, v in n_eval.items()}},
         "ms_per_frame": per_frame,
         "build_ms_per_edit": build_ms,
         "kernel_ms": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},

@@ -252,11 +252,17 @@ __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float 
     }
 }
 
-// 3-D DDA over the brick raster (the macrocell grid).  Cells are visited in
-// ray order; for a non-empty cell the exact slab interval of its box is
-// marched.  Boundary crossings are recomputed from integer plane positions
-// (no drift) and every axis only moves one way, so at most gx+gy+gz steps.
-// All state is in scalar registers.
+// ---------------------------------------------------------- walkers
+// A walker yields the hit intervals [ta, tb] of the non-empty regions of a
+// ray in ray order: the DDA over the brick raster (macrocell grid) or the
+// ordered traversal of a box tree.  The renderer alternates between a
+// collection phase, in which the walker's next intervals become sample-index
+// ranges (rule S, with the monotone cursor k_next; ranges that touch are
+// merged), and a marching phase over the collected ranges.  Lanes of a warp
+// therefore spend most of their time in the same phase, and samples are still
+// taken in increasing k exactly as interval-by-interval marching would take
+// them.
+
 __device__ __forceinline__ void dda_axis(float o, float d, float inv, bool zero, float p, int B,
                                          int g, int &c, int &step, float &tnext)
 {
@@ -274,45 +280,64 @@ __device__ __forceinline__ void dda_axis(float o, float d, float inv, bool zero,
     }
 }
 
-template <typename T, int SAMPLER>
-__device__ __forceinline__ void trace_grid(const RArgs &a, const Ray &r, float tn, float tf,
-                                           Acc &acc, long long &ns)
-{
-    const int B = a.B;
-    int cx, cy, cz, sx, sy, sz;
+// 3-D DDA over the brick raster.  Cells are visited in ray order; a
+// non-empty cell yields the exact slab interval of its box.  Boundary
+// crossings are recomputed from integer plane positions (no drift) and every
+// axis only moves one way, so at most gx+gy+gz steps.
+struct GridWalk {
+    int cx, cy, cz, sx, sy, sz, left;
     float tx, ty, tz;
-    dda_axis(r.o[0], r.d[0], r.inv[0], r.zero[0], fmaf(tn, r.d[0], r.o[0]), B, a.gx, cx, sx, tx);
-    dda_axis(r.o[1], r.d[1], r.inv[1], r.zero[1], fmaf(tn, r.d[1], r.o[1]), B, a.gy, cy, sy, ty);
-    dda_axis(r.o[2], r.d[2], r.inv[2], r.zero[2], fmaf(tn, r.d[2], r.o[2]), B, a.gz, cz, sz, tz);
-    int k_next = 0;
-    const int maxit = a.gx + a.gy + a.gz + 3;
-    for (int it = 0; it < maxit; ++it) {
-        if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
-            float lo[3] = {(float)(cx * B), (float)(cy * B), (float)(cz * B)};
-            float hi[3] = {(float)min((cx + 1) * B, a.nx), (float)min((cy + 1) * B, a.ny),
-                           (float)min((cz + 1) * B, a.nz)};
-            float ta = tn, tb = tf;
-            slab(r, lo, hi, ta, tb);
-            if (ta <= tb && march<T, SAMPLER>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
-        }
-        if (tx <= ty && tx <= tz) {
-            if (!(tx <= tf)) return;
-            cx += sx;
-            if (cx < 0 || cx >= a.gx) return;
-            tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
-        } else if (ty <= tz) {
-            if (!(ty <= tf)) return;
-            cy += sy;
-            if (cy < 0 || cy >= a.gy) return;
-            ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
-        } else {
-            if (!(tz <= tf)) return;
-            cz += sz;
-            if (cz < 0 || cz >= a.gz) return;
-            tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
-        }
+    bool done;
+
+    __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn)
+    {
+        dda_axis(r.o[0], r.d[0], r.inv[0], r.zero[0], fmaf(tn, r.d[0], r.o[0]), a.B, a.gx, cx, sx, tx);
+        dda_axis(r.o[1], r.d[1], r.inv[1], r.zero[1], fmaf(tn, r.d[1], r.o[1]), a.B, a.gy, cy, sy, ty);
+        dda_axis(r.o[2], r.d[2], r.inv[2], r.zero[2], fmaf(tn, r.d[2], r.o[2]), a.B, a.gz, cz, sz, tz);
+        left = a.gx + a.gy + a.gz + 3;
+        done = false;
     }
-}
+
+    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+                                         float &tb)
+    {
+        const int B = a.B;
+        bool hit = false;
+        while (!done && !hit) {
+            if (--left < 0) {
+                done = true;
+                break;
+            }
+            if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
+                float lo[3] = {(float)(cx * B), (float)(cy * B), (float)(cz * B)};
+                float hi[3] = {(float)min((cx + 1) * B, a.nx), (float)min((cy + 1) * B, a.ny),
+                               (float)min((cz + 1) * B, a.nz)};
+                ta = tn;
+                tb = tf;
+                slab(r, lo, hi, ta, tb);
+                hit = ta <= tb;
+            }
+            // step to the next cell
+            if (tx <= ty && tx <= tz) {
+                if (!(tx <= tf)) done = true;
+                cx += sx;
+                if (cx < 0 || cx >= a.gx) done = true;
+                tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
+            } else if (ty <= tz) {
+                if (!(ty <= tf)) done = true;
+                cy += sy;
+                if (cy < 0 || cy >= a.gy) done = true;
+                ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
+            } else {
+                if (!(tz <= tf)) done = true;
+                cz += sz;
+                if (cz < 0 || cz >= a.gz) done = true;
+                tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
+            }
+        }
+        return hit;
+    }
+};
 
 // Box in brick coordinates [lo, hi) -> closed voxel-space box, clamped at the
 // volume's far faces (partial bricks).
@@ -342,46 +367,67 @@ __device__ __forceinline__ void leaf_box_f(const RArgs &a, int KIND, int32_t ref
 }
 
 // Ordered traversal of a binary box tree.  Each inner node carries both
-// children's boxes; both are slab-tested, the child entered first is
-// visited first and the other is pushed (LBVH children are separated by the
-// Morton split plane and k-d children by the split plane, so entry order is
-// front-to-back order).  A leaf's box interval is marched with rule S.  The
-// stack of STACK entries suffices because the build guarantees a height of at
-// most STACK + 1 levels (30-bit Morton keys give LBVH heights <= 31).
-template <typename T, int SAMPLER, int KIND, int STACK>
-__device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float tn, float tf,
-                                           Acc &acc, long long &ns)
-{
-    const int n = __ldg(a.count);
-    if (n <= 0) return;
-    // reference bounds: a valid tree never leaves them and visits each node at
-    // most once per ray; the checks keep a corrupt structure from reading
-    // outside its buffers or looping
-    const int n_inner = KIND == ESS_LBVH ? n - 1 : n;
-    const int64_t n_leaf = KIND == ESS_LBVH ? (int64_t)a.gx * a.gy * a.gz : n;
-    int budget = 2 * n + 1;
-    int32_t ref = __ldg(a.root);
+// children's boxes; both are slab-tested, the child entered first is visited
+// first and the other is pushed (LBVH children are separated by the Morton
+// split plane and k-d children by the split plane, so entry order is
+// front-to-back order).  A leaf yields its box interval.  The stack of STACK
+// entries suffices because the build guarantees a height of at most STACK + 1
+// levels (30-bit Morton keys give LBVH heights <= 31).  Reference and
+// iteration bounds keep a corrupt structure from reading outside its buffers
+// or looping; a valid tree never reaches them.
+template <int KIND, int STACK> struct TreeWalk {
+    int32_t stack[STACK];
+    int sp, budget, n_inner;
+    int64_t n_leaf;
+    int32_t ref;
+    bool done;
+
+    __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn, float tf)
     {
+        const int n = __ldg(a.count);
+        done = true;
+        if (n <= 0) return;
+        n_inner = KIND == ESS_LBVH ? n - 1 : n;
+        n_leaf = KIND == ESS_LBVH ? (int64_t)a.gx * a.gy * a.gz : n;
+        budget = 2 * n + 1;
+        ref = __ldg(a.root);
+        sp = 0;
         float lo[3], hi[3];
         brick_box_f(a, __ldg(a.root + 1), __ldg(a.root + 2), __ldg(a.root + 3), __ldg(a.root + 4),
                     __ldg(a.root + 5), __ldg(a.root + 6), lo, hi);
         float ta = tn, tb = tf;
         slab(r, lo, hi, ta, tb);
-        if (!(ta <= tb)) return;
+        done = !(ta <= tb);
     }
-    int32_t stack[STACK];
-    int sp = 0;
-    int k_next = 0;
-    while (--budget >= 0) {
-        if (ref < 0) {
-            if (-1 - (int64_t)ref >= n_leaf) return;
-            float lo[3], hi[3];
-            leaf_box_f(a, KIND, ref, lo, hi);
-            float ta = tn, tb = tf;
-            slab(r, lo, hi, ta, tb);
-            if (ta <= tb && march<T, SAMPLER>(a, r, tn, tf, ta, tb, k_next, acc, ns)) return;
-        } else {
-            if (ref >= n_inner) return;
+
+    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+                                         float &tb)
+    {
+        bool hit = false;
+        while (!done && !hit) {
+            if (--budget < 0) {
+                done = true;
+                break;
+            }
+            if (ref < 0) {
+                if (-1 - (int64_t)ref < n_leaf) {
+                    float lo[3], hi[3];
+                    leaf_box_f(a, KIND, ref, lo, hi);
+                    ta = tn;
+                    tb = tf;
+                    slab(r, lo, hi, ta, tb);
+                    hit = ta <= tb;
+                } else {
+                    done = true;
+                }
+                if (sp == 0) done = true;
+                else ref = stack[--sp];
+                continue;
+            }
+            if (ref >= n_inner) {
+                done = true;
+                break;
+            }
             const uint4 *q = reinterpret_cast<const uint4 *>(a.nodes + ref);
             uint4 q0 = __ldg(q), q1 = __ldg(q + 1);
             // lbox = q0.x..q0.z (6 x u16), rbox = q0.w, q1.x, q1.y; left = q1.z, right = q1.w
@@ -399,19 +445,101 @@ __device__ __forceinline__ void trace_tree(const RArgs &a, const Ray &r, float t
                 bool left_first = la <= ra;
                 if (sp < STACK) stack[sp++] = left_first ? rc : lc;
                 ref = left_first ? lc : rc;
-                continue;
-            }
-            if (hl) {
+            } else if (hl) {
                 ref = lc;
-                continue;
-            }
-            if (hr) {
+            } else if (hr) {
                 ref = rc;
-                continue;
+            } else if (sp == 0) {
+                done = true;
+            } else {
+                ref = stack[--sp];
             }
         }
-        if (sp == 0) return;
-        ref = stack[--sp];
+        return hit;
+    }
+};
+
+// Collected sample ranges (at most RANGES), kept in registers.  A phase also
+// stops once it holds LOOKAHEAD samples, so that early ray termination wastes
+// little traversal.
+constexpr int RANGES = 4;
+constexpr int LOOKAHEAD = 48;
+
+__device__ __forceinline__ int2 range_get(const int2 (&rg)[RANGES], int i)
+{
+    int2 v = rg[0];
+#pragma unroll
+    for (int j = 1; j < RANGES; ++j)
+        if (i == j) v = rg[j];
+    return v;
+}
+
+// Interval-by-interval skipping with phases: collect, then march.  The outer
+// loop is uniform over the lanes that entered together (__any_sync), and the
+// inner loops have single exits, so the warp reconverges at every phase
+// boundary.
+template <typename T, int SAMPLER, typename Walk>
+__device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float tn, float tf,
+                                           Walk &w, Acc &acc, long long &ns)
+{
+    const unsigned lanes = __activemask();
+    int k_next = 0;
+    bool alive = true;
+    while (__any_sync(lanes, alive)) {
+        int2 rg[RANGES];
+        int nr = 0;
+        if (alive) {
+            int held = 0;
+            float ta, tb;
+            while (nr < RANGES && held < LOOKAHEAD) {
+                if (!w.next(a, r, tn, tf, ta, tb)) break;
+                float ka = ceilf((ta - tn) / a.dt) - 1.0f;
+                float kb = floorf((tb - tn) / a.dt) + 1.0f;
+                kb = kb < 16777216.0f ? kb : 16777216.0f;
+                int k0 = ka > (float)k_next ? (int)ka : k_next;
+                int k1 = (int)kb;
+                if (k1 >= k0) {
+                    bool merge = nr > 0 && k0 == k_next;  // touches the previous range
+#pragma unroll
+                    for (int j = 0; j < RANGES; ++j) {
+                        if (merge && j == nr - 1) rg[j].y = k1;
+                        if (!merge && j == nr) rg[j] = make_int2(k0, k1);
+                    }
+                    if (!merge) ++nr;
+                    held += k1 - k0 + 1;
+                    k_next = k1 + 1;
+                }
+            }
+            if (nr == 0) alive = false;
+        }
+        if (alive) {
+            // march the collected ranges in increasing k
+            int i = 0;
+            int2 cur = rg[0];
+            int k = cur.x;
+            float kf = (float)k;
+            while (true) {
+                float t = fmaf(kf, a.dt, tn);
+                if (!(t < tf)) {
+                    alive = false;
+                    break;
+                }
+                ++ns;
+                if (sample_step<T, SAMPLER>(a, r, t, acc)) {
+                    alive = false;
+                    break;
+                }
+                if (k == cur.y) {
+                    if (++i >= nr) break;
+                    cur = range_get(rg, i);
+                    k = cur.x;
+                    kf = (float)k;
+                } else {
+                    ++k;
+                    kf += 1.0f;
+                }
+            }
+        }
     }
 }
 
@@ -429,14 +557,21 @@ __device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long 
     slab(r, lo, hi, tn, tf);
     Acc acc = {0.0f, 0.0f, 0.0f, 0.0f};
     if (tn < tf) {
-        if (KIND == ESS_NONE)
+        if (KIND == ESS_NONE) {
             trace_naive<T, SAMPLER>(a, r, tn, tf, acc, ns);
-        else if (KIND == ESS_GRID)
-            trace_grid<T, SAMPLER>(a, r, tn, tf, acc, ns);
-        else if (KIND == ESS_LBVH)
-            trace_tree<T, SAMPLER, ESS_LBVH, 32>(a, r, tn, tf, acc, ns);
-        else
-            trace_tree<T, SAMPLER, ESS_KD, 128>(a, r, tn, tf, acc, ns);
+        } else if (KIND == ESS_GRID) {
+            GridWalk w;
+            w.init(a, r, tn);
+            trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
+        } else if (KIND == ESS_LBVH) {
+            TreeWalk<ESS_LBVH, 32> w;
+            w.init(a, r, tn, tf);
+            trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
+        } else {
+            TreeWalk<ESS_KD, 128> w;
+            w.init(a, r, tn, tf);
+            trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
+        }
     }
     float one_m = 1.0f - acc.a;
     a.out[(size_t)y * a.W + x] =
