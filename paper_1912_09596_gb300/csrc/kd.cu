@@ -102,10 +102,20 @@ __device__ __forceinline__ void brick_coords(uint32_t b, int gx, int gy, int c[3
     c[2] = (int)(b / ((uint32_t)gx * (uint32_t)gy));
 }
 
-__device__ __forceinline__ void slab_reset(int32_t *slot)
+// A slab box is stored as 6 ints that only ever grow: 65536 - lo (per axis)
+// and hi, so that every update is an atomicMax and an empty slab is all zeros
+// (brick coordinates are below 65536).
+constexpr int32_t KD_LO_BIAS = 65536;
+
+// Decodes a stored slab into a box; returns false for an empty slab.
+__device__ __forceinline__ bool slab_load(const int32_t *e, int32_t box[6])
 {
-    slot[0] = slot[1] = slot[2] = INT_MAX;
-    slot[3] = slot[4] = slot[5] = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        box[k] = KD_LO_BIAS - e[k];
+        box[3 + k] = e[3 + k];
+    }
+    return e[0] != 0;
 }
 
 // Level state, in device memory so that the level loop can run without the
@@ -185,20 +195,41 @@ __global__ void k_kd_init(const int *__restrict__ count, const int32_t *__restri
         nodes9[7] = 0;
         nodes9[8] = -1;
     }
-    for (int s = t; s < 3 * S; s += blockDim.x) slab_reset(slabs0 + 6 * s);
+    for (int s = t; s < 3 * S * 6; s += blockDim.x) slabs0[s] = 0;
 }
 
 // ------------------------------------------------------------ per level
 // Moves each brick of a node split on the previous level into its child,
 // then adds the brick to the slab boxes of its node if that node is on the
-// current level.
-__global__ void k_kd_accumulate(const uint32_t *__restrict__ ids, const int *__restrict__ count,
-                                int *__restrict__ brick_node, const int32_t *__restrict__ nodes9,
-                                int32_t *slabs0, int32_t *slabs1, const KdState *st, KdParams P)
+// current level.  Updates are combined first: a whole warp on one slab
+// reduces with warp intrinsics, otherwise a block-local hash table of slabs
+// in shared memory takes the min/max, and each block then applies one set of
+// global atomics per distinct slab (min/max are order independent, so the
+// result is the same as with direct atomics).
+constexpr int KD_HT = 128;  // shared hash slots per block
+
+__device__ __forceinline__ void slab_atomic(int32_t *slot, const int v[6])
 {
+    for (int k = 0; k < 6; ++k) atomicMax(slot + k, v[k]);
+}
+
+__global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restrict__ ids,
+                                                       const int *__restrict__ count,
+                                                       int *__restrict__ brick_node,
+                                                       const int32_t *__restrict__ nodes9,
+                                                       int32_t *slabs0, int32_t *slabs1,
+                                                       const KdState *st, KdParams P)
+{
+    __shared__ long long s_key[KD_HT];
+    __shared__ int s_val[KD_HT][6];
     const int prev_begin = st->prev_begin, lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
-    if (lvl_size <= 0) return;
+    if (lvl_size <= 0) return;  // uniform
     int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
+    for (int h = threadIdx.x; h < KD_HT; h += blockDim.x) {
+        s_key[h] = -1;
+        for (int k = 0; k < 6; ++k) s_val[h][k] = 0;
+    }
+    __syncthreads();
     int n = *count;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool live = i < n;
@@ -221,37 +252,41 @@ __global__ void k_kd_accumulate(const uint32_t *__restrict__ ids, const int *__r
     }
     const int32_t *box = nodes9 + 9 * (size_t)(live ? node : 0);
     int local = node - lvl_begin;
+    const int v[6] = {KD_LO_BIAS - c[0], KD_LO_BIAS - c[1], KD_LO_BIAS - c[2],
+                      c[0] + 1, c[1] + 1, c[2] + 1};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         bool use = live && box[3 + a] - box[a] >= 2;
         int s = use ? kd_slab_of(c[a], box[a], box[3 + a], P.nbins) : 0;
         long long slot_id = use ? ((long long)local * 3 + a) * P.S + s : -1;
-        // near the root whole warps update the same slab: reduce in the warp
-        // and let one lane do the atomics (min/max are order independent)
         long long first = __shfl_sync(0xffffffffu, slot_id, 0);
         if (__all_sync(0xffffffffu, slot_id == first)) {
             if (first < 0) continue;
-            int v[6] = {c[0], c[1], c[2], c[0] + 1, c[1] + 1, c[2] + 1};
+            int r[6];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                v[k] = __reduce_min_sync(0xffffffffu, v[k]);
-                v[3 + k] = __reduce_max_sync(0xffffffffu, v[3 + k]);
-            }
-            if ((threadIdx.x & 31) == 0) {
-                int32_t *slot = slabs + 6 * first;
-                for (int k = 0; k < 3; ++k) {
-                    atomicMin(slot + k, v[k]);
-                    atomicMax(slot + 3 + k, v[3 + k]);
+            for (int k = 0; k < 6; ++k) r[k] = __reduce_max_sync(0xffffffffu, v[k]);
+            if ((threadIdx.x & 31) == 0) slab_atomic(slabs + 6 * first, r);
+        } else if (use) {
+            int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> 57);  // 7 bits
+            bool done = false;
+            for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (KD_HT - 1)) {
+                long long old = atomicCAS((unsigned long long *)&s_key[h], (unsigned long long)-1ll,
+                                          (unsigned long long)slot_id);
+                if (old == -1 || old == slot_id) {
+                    for (int k = 0; k < 6; ++k) atomicMax(&s_val[h][k], v[k]);
+                    done = true;
                 }
             }
-        } else if (use) {
-            int32_t *slot = slabs + 6 * slot_id;
-            atomicMin(slot + 0, c[0]);
-            atomicMin(slot + 1, c[1]);
-            atomicMin(slot + 2, c[2]);
-            atomicMax(slot + 3, c[0] + 1);
-            atomicMax(slot + 4, c[1] + 1);
-            atomicMax(slot + 5, c[2] + 1);
+            if (!done) slab_atomic(slabs + 6 * slot_id, v);
+        }
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < KD_HT; h += blockDim.x) {
+        long long key = s_key[h];
+        if (key >= 0) {
+            int r[6];
+            for (int k = 0; k < 6; ++k) r[k] = s_val[h][k];
+            slab_atomic(slabs + 6 * key, r);
         }
     }
 }
@@ -267,14 +302,30 @@ __device__ __forceinline__ void box_union(int32_t *acc, const int32_t *s)
 
 // One thread per node of the level: cost of every candidate from prefix and
 // suffix unions of the slab boxes, then the split rule.  `vr` is scratch for
-// suffix volumes.  Writes the decision and the block's split count.
+// suffix volumes.  Writes the decision and the block's split count.  Before
+// that, all threads of the grid zero the slab region the next level will use
+// (at most two children per node) with 8-byte stores.  With SF > 0 the number
+// of slab slots is the compile-time constant SF (the 4-bin case), so the slab
+// loops unroll and their loads are independent.
+template <int SF>
 __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ nodes9,
                                                    int32_t *slabs0, int32_t *slabs1,
                                                    unsigned long long *vr, KdDecision *dec,
                                                    uint32_t *block_sums, const KdState *st,
-                                                   KdParams P)
+                                                   KdParams P, int next_cap)
 {
+    const int S = SF > 0 ? SF : P.S;
     const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if (lvl_size <= 0) return;  // uniform
+    {
+        // the next level has at most min(2 lvl_size, capacity) nodes
+        int2 *next = reinterpret_cast<int2 *>(kd_next_slabs(slabs0, slabs1, st));
+        size_t nodes = (size_t)min(2 * lvl_size, next_cap);
+        size_t words = nodes * 9 * S;  // 18 S ints per node
+        size_t stride = (size_t)gridDim.x * blockDim.x;
+        for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < words; q += stride)
+            next[q] = make_int2(0, 0);
+    }
     if ((int)(blockIdx.x * blockDim.x) >= lvl_size) return;  // uniform per block
     const int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
     int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,16 +341,28 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
                 int lo = X[a], hi = X[3 + a];
                 if (hi - lo < 2) continue;
                 int ns = kd_slabs(lo, hi, P.nbins);
-                const int32_t *sl = slabs + 6 * ((size_t)l * 3 + a) * P.S;
-                unsigned long long *v = vr + ((size_t)l * 3 + a) * P.S;
+                const int32_t *sl = slabs + 6 * ((size_t)l * 3 + a) * S;
+                unsigned long long *v = vr + ((size_t)l * 3 + a) * S;
                 int32_t acc[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-                for (int j = ns - 1; j >= 1; --j) {
-                    box_union(acc, sl + 6 * j);
-                    v[j] = acc[0] == INT_MAX ? ~0ull : kd_volume(acc, P);
+                if (SF > 0) {
+#pragma unroll
+                    for (int j = (SF > 0 ? SF : 1) - 1; j >= 1; --j) {
+                        if (j >= ns) continue;
+                        int32_t b[6];
+                        if (slab_load(sl + 6 * j, b)) box_union(acc, b);
+                        v[j] = acc[0] == INT_MAX ? ~0ull : kd_volume(acc, P);
+                    }
+                } else {
+                    for (int j = ns - 1; j >= 1; --j) {
+                        int32_t b[6];
+                        if (slab_load(sl + 6 * j, b)) box_union(acc, b);
+                        v[j] = acc[0] == INT_MAX ? ~0ull : kd_volume(acc, P);
+                    }
                 }
                 int32_t pre[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
                 for (int j = 1; j < ns; ++j) {
-                    box_union(pre, sl + 6 * (j - 1));
+                    int32_t b[6];
+                    if (slab_load(sl + 6 * (j - 1), b)) box_union(pre, b);
                     // both sides are non-empty for a tight node box; the test
                     // only guards the definition
                     if (pre[0] == INT_MAX || v[j] == ~0ull) continue;
@@ -338,10 +401,15 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
         if (bax >= 0) {
             int lo = X[bax], hi = X[3 + bax];
             int ns = kd_slabs(lo, hi, P.nbins);
-            const int32_t *sl = slabs + 6 * ((size_t)l * 3 + bax) * P.S;
+            const int32_t *sl = slabs + 6 * ((size_t)l * 3 + bax) * S;
             int32_t L[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
             int32_t R[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-            for (int j = 0; j < ns; ++j) box_union(j < bj ? L : R, sl + 6 * j);
+            for (int j = 0; j < ns; ++j) {
+                int32_t b[6];
+                if (!slab_load(sl + 6 * j, b)) continue;
+                if (j < bj) box_union(L, b);
+                else box_union(R, b);
+            }
             if (L[0] != INT_MAX && R[0] != INT_MAX) {
                 d.split = 1;
                 d.axis = bax;
@@ -398,9 +466,9 @@ __global__ void __launch_bounds__(1024) k_kd_scan(uint32_t *block_sums, KdState 
     if (t == 0) st->splits = (int)carry;
 }
 
-// Writes split decisions into the node records, creates the children (BFS
-// numbering: after all nodes of this level, in node order, left first) and
-// resets their slabs for the next level.
+// Writes split decisions into the node records and creates the children
+// (BFS numbering: after all nodes of this level, in node order, left first);
+// their slabs were zeroed by the decide kernel.
 __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ dec,
                                                  const uint32_t *__restrict__ block_off,
                                                  int32_t *nodes9, int32_t *slabs0, int32_t *slabs1,
@@ -409,7 +477,6 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
 {
     const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
     if ((int)(blockIdx.x * blockDim.x) >= lvl_size) return;  // uniform per block
-    int32_t *next_slabs = kd_next_slabs(slabs0, slabs1, st);
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     int split = l < lvl_size ? dec[l].split : 0;
     // block-local exclusive rank of the split flag
@@ -442,10 +509,6 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
     cl[6] = cr[6] = -1;
     cl[7] = cr[7] = 0;
     cl[8] = cr[8] = -1;
-    for (int s = 0; s < 3 * S; ++s) {
-        slab_reset(next_slabs + 6 * ((size_t)(2 * rank) * 3 * S + s));
-        slab_reset(next_slabs + 6 * ((size_t)(2 * rank + 1) * 3 * S + s));
-    }
 }
 
 // Moves the level state on; in the graph build it also decides on the device
@@ -579,13 +642,20 @@ static void kd_root_launches(Ctx &c, Structure &s, const KdParams &P, unsigned b
 
 // One level: accumulate, decide, scan, emit, advance.
 static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks,
-                              unsigned node_blocks, cudaGraphConditionalHandle h, int use_handle)
+                              unsigned node_blocks, int next_cap, cudaGraphConditionalHandle h,
+                              int use_handle)
 {
     KdState *st = (KdState *)s.kd_state;
     k_kd_accumulate<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node, s.kd_nodes,
                                                         s.kd_slabs[0], s.kd_slabs[1], st, P);
-    k_kd_decide<<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], s.kd_vr,
-                                                   (KdDecision *)s.kd_dec, s.kd_block_sums, st, P);
+    if (P.S == 4)
+        k_kd_decide<4><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
+                                                          s.kd_vr, (KdDecision *)s.kd_dec,
+                                                          s.kd_block_sums, st, P, next_cap);
+    else
+        k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
+                                                          s.kd_vr, (KdDecision *)s.kd_dec,
+                                                          s.kd_block_sums, st, P, next_cap);
     k_kd_scan<<<1, 1024, 0, c.stream>>>(s.kd_block_sums, st);
     k_kd_emit<<<node_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
                                                  s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], P.S,
@@ -657,7 +727,8 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
-        kd_level_launches(c, s, P, brick_blocks, node_blocks, h, 1);
+        kd_level_launches(c, s, P, brick_blocks, node_blocks,
+                          (int)std::min(s.kd_slab_cap[0], s.kd_slab_cap[1]), h, 1);
         ESS_CUDA(cudaStreamEndCapture(c.stream, &body));
         // traversal layout after the loop
         ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, g, &loop, nullptr, 1,
@@ -714,7 +785,7 @@ void launch_kd(Ctx &c, Structure &s)
         unsigned nblk = (unsigned)((lvl_size + 255) / 256);
         {
             Launch L(c, "kd_level");
-            kd_level_launches(c, s, P, brick_blocks, nblk, 0, 0);
+            kd_level_launches(c, s, P, brick_blocks, nblk, (int)s.kd_slab_cap[cur ^ 1], 0, 0);
         }
         ESS_CUDA(cudaMemcpyAsync(&hs, s.kd_state, sizeof(KdState), cudaMemcpyDeviceToHost,
                                  c.stream));
