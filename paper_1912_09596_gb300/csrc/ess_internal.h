@@ -44,16 +44,18 @@ struct Error {
     } while (0)
 
 // ---------------------------------------------------- device-side layouts
-// Node of a binary box tree (LBVH and k-d share it): both children's boxes
-// live in the parent so one 32-byte load feeds both slab tests.  Boxes are in
-// brick coordinates, hi exclusive.  child >= 0: inner node; child < 0: leaf,
-// payload -1 - child (LBVH: brick id; k-d: leaf index).
+// Traversal node of a binary box tree (LBVH and k-d share it): both
+// children's boxes live in the parent, as floats in voxel units (brick
+// coordinates times the brick size; the far faces are not clamped to the
+// volume, which only makes the boxes larger), so that four 16-byte loads feed
+// both slab tests with no decoding.  child >= 0: inner node; child < 0: leaf,
+// payload -1 - child (LBVH: brick id; k-d: node id).
 struct __align__(16) BoxNode {
-    uint16_t lbox[6];
-    uint16_t rbox[6];
-    int32_t left, right;
+    float lbox[6];  // lo xyz, hi xyz
+    float rbox[6];
+    int32_t left, right, pad0, pad1;
 };
-static_assert(sizeof(BoxNode) == 32, "BoxNode must be 32 bytes");
+static_assert(sizeof(BoxNode) == 64, "BoxNode must be 64 bytes");
 
 // ------------------------------------------------------------------ objects
 struct Ctx;
@@ -106,7 +108,7 @@ struct Structure {
     int32_t *inner_box = nullptr;  // (n-1) x 6
     int *arrive = nullptr;
     BoxNode *nodes = nullptr;      // traversal nodes (LBVH: n-1; k-d: inner nodes)
-    int32_t *root = nullptr;       // device root record: ref, box lo xyz, hi xyz, pad
+    int32_t *root = nullptr;       // device root record: ref, then the box as 6 floats (voxels)
     int height = 0;
     // k-d
     Volume *volume = nullptr;

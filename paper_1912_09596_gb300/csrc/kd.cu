@@ -537,7 +537,7 @@ __global__ void k_kd_advance(KdState *st, int capacity, int max_levels, uint32_t
 // Traversal layout: one BoxNode per node id (leaf entries unused), children
 // referenced as node ids, leaves as -1 - id; the root record and node count.
 __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const KdState *st, int *m_dev,
-                          BoxNode *nodes, int32_t *root)
+                          BoxNode *nodes, int32_t *root, int B)
 {
     int m = st->lvl_begin;  // all levels done: every node id is below this
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,18 +546,19 @@ __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const KdState *st,
     const int32_t *rec = nodes9 + 9 * (size_t)i;
     if (i == 0) {
         root[0] = rec[8] >= 0 ? 0 : -1;
-        for (int a = 0; a < 6; ++a) root[1 + a] = rec[a];
+        for (int a = 0; a < 6; ++a) root[1 + a] = __float_as_int((float)(rec[a] * B));
     }
     int fc = rec[8];
     if (fc < 0) return;
     const int32_t *L = nodes9 + 9 * (size_t)fc, *R = L + 9;
     BoxNode nd;
     for (int a = 0; a < 6; ++a) {
-        nd.lbox[a] = (uint16_t)L[a];
-        nd.rbox[a] = (uint16_t)R[a];
+        nd.lbox[a] = (float)(L[a] * B);
+        nd.rbox[a] = (float)(R[a] * B);
     }
     nd.left = L[8] >= 0 ? fc : -1 - fc;
     nd.right = R[8] >= 0 ? fc + 1 : -1 - (fc + 1);
+    nd.pad0 = nd.pad1 = 0;
     nodes[i] = nd;
 }
 
@@ -734,7 +735,7 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
         ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, g, &loop, nullptr, 1,
                                                cudaStreamCaptureModeThreadLocal));
         k_kd_pack<<<(unsigned)((2 * cap + 255) / 256), 256, 0, c.stream>>>(
-            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root);
+            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root, P.B);
         ESS_CUDA(cudaStreamEndCapture(c.stream, &g));
         ESS_CUDA(cudaGraphInstantiate(&s.kd_exec, g, 0));
     } catch (...) {
@@ -797,7 +798,7 @@ void launch_kd(Ctx &c, Structure &s)
     {
         Launch L(c, "kd_pack");
         k_kd_pack<<<(unsigned)((hs.lvl_begin + 255) / 256 + 1), 256, 0, c.stream>>>(
-            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root);
+            s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root, P.B);
     }
 }
 

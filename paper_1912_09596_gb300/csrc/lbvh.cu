@@ -280,11 +280,20 @@ __device__ __forceinline__ void brick_box(uint32_t b, int gx, int gy, int32_t bo
     box[3] = x + 1; box[4] = y + 1; box[5] = z + 1;
 }
 
+// root record: ref, then the box in voxel units as float bits
+__device__ __forceinline__ void write_root(int32_t *root, int32_t ref, const int32_t box[6], int B)
+{
+    root[0] = ref;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) root[1 + a] = __float_as_int((float)(box[a] * B));
+}
+
 __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int *__restrict__ count,
                               const int32_t *__restrict__ left, const int32_t *__restrict__ right,
                               const int32_t *__restrict__ parent,
                               const int32_t *__restrict__ leaf_parent, int *arrive,
-                              int32_t *inner_box, BoxNode *nodes, int32_t *root, int gx, int gy)
+                              int32_t *inner_box, BoxNode *nodes, int32_t *root, int gx, int gy,
+                              int B)
 {
     int n = *count;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -293,9 +302,7 @@ __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int
     brick_box(sorted_ids[j], gx, gy, box);
     if (n == 1) {
         // a single non-empty brick: the root is that leaf
-        root[0] = -1 - (int32_t)sorted_ids[0];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) root[1 + a] = box[a];
+        write_root(root, -1 - (int32_t)sorted_ids[0], box, B);
         return;
     }
     int p = leaf_parent[j];
@@ -327,17 +334,14 @@ __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
             inner_box[6 * p + a] = box[a];
-            nd.lbox[a] = (uint16_t)lb[a];
-            nd.rbox[a] = (uint16_t)rb[a];
+            nd.lbox[a] = (float)(lb[a] * B);
+            nd.rbox[a] = (float)(rb[a] * B);
         }
         nd.left = lc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - lc)) : lc;
         nd.right = rc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - rc)) : rc;
+        nd.pad0 = nd.pad1 = 0;
         nodes[p] = nd;
-        if (p == 0) {
-            root[0] = 0;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) root[1 + a] = box[a];
-        }
+        if (p == 0) write_root(root, 0, box, B);
         p = __ldcg(parent + p);
     }
 }
@@ -388,7 +392,8 @@ void launch_lbvh(Ctx &c, Structure &s)
         Launch L(c, "lbvh_bounds");
         k_lbvh_bounds<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
                                                     s.parent, s.leaf_parent, s.arrive,
-                                                    s.inner_box, s.nodes, s.root, s.gx, s.gy);
+                                                    s.inner_box, s.nodes, s.root, s.gx, s.gy,
+                                                    s.p.brick);
     }
 }
 

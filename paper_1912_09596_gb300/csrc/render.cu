@@ -38,9 +38,8 @@ struct RArgs {
     int B, gx, gy, gz;
     // box trees (LBVH, k-d)
     const BoxNode *nodes;
-    const int32_t *root;      // ref, box lo xyz, hi xyz (brick coordinates)
+    const int32_t *root;      // ref, then the root box as 6 floats (voxels)
     const int *count;         // > 0 iff the tree is non-empty
-    const int32_t *kd_nodes;  // k-d: node records, 9 ints (box first)
     unsigned long long *samples;
 };
 
@@ -280,13 +279,17 @@ __device__ __forceinline__ void dda_axis(float o, float d, float inv, bool zero,
     }
 }
 
-// 3-D DDA over the brick raster.  Cells are visited in ray order; a
-// non-empty cell yields the exact slab interval of its box.  Boundary
-// crossings are recomputed from integer plane positions (no drift) and every
-// axis only moves one way, so at most gx+gy+gz steps.
+// 3-D DDA over the brick raster.  Cells are visited in ray order and the
+// boundary crossings of consecutive cells tile [t_near, t_far); a non-empty
+// cell yields the span between its entry and exit crossing.  (A crossing
+// rounded to the wrong side of a corner only moves a sample whose cell is in
+// doubt, and such a sample is within half a voxel of both cells, so its
+// opacity is zero unless both are non-empty.)  Crossings are recomputed from
+// integer plane positions (no drift) and every axis only moves one way, so at
+// most gx+gy+gz steps.
 struct GridWalk {
     int cx, cy, cz, sx, sy, sz, left;
-    float tx, ty, tz;
+    float tx, ty, tz, tcur;
     bool done;
 
     __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn)
@@ -295,6 +298,7 @@ struct GridWalk {
         dda_axis(r.o[1], r.d[1], r.inv[1], r.zero[1], fmaf(tn, r.d[1], r.o[1]), a.B, a.gy, cy, sy, ty);
         dda_axis(r.o[2], r.d[2], r.inv[2], r.zero[2], fmaf(tn, r.d[2], r.o[2]), a.B, a.gz, cz, sz, tz);
         left = a.gx + a.gy + a.gz + 3;
+        tcur = tn;
         done = false;
     }
 
@@ -308,78 +312,49 @@ struct GridWalk {
                 done = true;
                 break;
             }
+            float texit = fminf(tx, fminf(ty, tz));
             if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
-                float lo[3] = {(float)(cx * B), (float)(cy * B), (float)(cz * B)};
-                float hi[3] = {(float)min((cx + 1) * B, a.nx), (float)min((cy + 1) * B, a.ny),
-                               (float)min((cz + 1) * B, a.nz)};
-                ta = tn;
-                tb = tf;
-                slab(r, lo, hi, ta, tb);
-                hit = ta <= tb;
+                ta = tcur;
+                tb = fminf(texit, tf);
+                hit = true;
             }
-            // step to the next cell
+            if (!(texit <= tf)) done = true;
             if (tx <= ty && tx <= tz) {
-                if (!(tx <= tf)) done = true;
                 cx += sx;
                 if (cx < 0 || cx >= a.gx) done = true;
                 tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
             } else if (ty <= tz) {
-                if (!(ty <= tf)) done = true;
                 cy += sy;
                 if (cy < 0 || cy >= a.gy) done = true;
                 ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
             } else {
-                if (!(tz <= tf)) done = true;
                 cz += sz;
                 if (cz < 0 || cz >= a.gz) done = true;
                 tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
             }
+            tcur = texit;
         }
         return hit;
     }
 };
 
-// Box in brick coordinates [lo, hi) -> closed voxel-space box, clamped at the
-// volume's far faces (partial bricks).
-__device__ __forceinline__ void brick_box_f(const RArgs &a, int lx, int ly, int lz, int hx, int hy,
-                                            int hz, float lo[3], float hi[3])
-{
-    lo[0] = (float)(lx * a.B);
-    lo[1] = (float)(ly * a.B);
-    lo[2] = (float)(lz * a.B);
-    hi[0] = (float)min(hx * a.B, a.nx);
-    hi[1] = (float)min(hy * a.B, a.ny);
-    hi[2] = (float)min(hz * a.B, a.nz);
-}
-
-__device__ __forceinline__ void leaf_box_f(const RArgs &a, int KIND, int32_t ref, float lo[3],
-                                           float hi[3])
-{
-    int32_t id = -1 - ref;
-    if (KIND == ESS_LBVH) {
-        int x = id % a.gx, y = (id / a.gx) % a.gy, z = id / (a.gx * a.gy);
-        brick_box_f(a, x, y, z, x + 1, y + 1, z + 1, lo, hi);
-    } else {
-        const int32_t *b = a.kd_nodes + 9 * (size_t)id;
-        brick_box_f(a, __ldg(b), __ldg(b + 1), __ldg(b + 2), __ldg(b + 3), __ldg(b + 4),
-                    __ldg(b + 5), lo, hi);
-    }
-}
-
 // Ordered traversal of a binary box tree.  Each inner node carries both
-// children's boxes; both are slab-tested, the child entered first is visited
-// first and the other is pushed (LBVH children are separated by the Morton
-// split plane and k-d children by the split plane, so entry order is
-// front-to-back order).  A leaf yields its box interval.  The stack of STACK
-// entries suffices because the build guarantees a height of at most STACK + 1
-// levels (30-bit Morton keys give LBVH heights <= 31).  Reference and
-// iteration bounds keep a corrupt structure from reading outside its buffers
-// or looping; a valid tree never reaches them.
+// children's boxes (floats, voxel units); both are slab-tested, the child
+// entered first is visited first and the other is pushed with its interval
+// (LBVH children are separated by the Morton split plane and k-d children by
+// the split plane, so entry order is front-to-back order).  A leaf yields the
+// interval its parent computed for it, so leaves cost no further work.  The
+// stack of STACK entries suffices because the build guarantees a height of at
+// most STACK + 1 levels (30-bit Morton keys give LBVH heights <= 31).
+// Reference and iteration bounds keep a corrupt structure from reading
+// outside its buffers or looping; a valid tree never reaches them.
 template <int KIND, int STACK> struct TreeWalk {
-    int32_t stack[STACK];
+    int32_t sref[STACK];
+    float sta[STACK], stb[STACK];
     int sp, budget, n_inner;
     int64_t n_leaf;
     int32_t ref;
+    float cta, ctb;  // interval of `ref` (used when it is a leaf)
     bool done;
 
     __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn, float tf)
@@ -393,11 +368,27 @@ template <int KIND, int STACK> struct TreeWalk {
         ref = __ldg(a.root);
         sp = 0;
         float lo[3], hi[3];
-        brick_box_f(a, __ldg(a.root + 1), __ldg(a.root + 2), __ldg(a.root + 3), __ldg(a.root + 4),
-                    __ldg(a.root + 5), __ldg(a.root + 6), lo, hi);
-        float ta = tn, tb = tf;
-        slab(r, lo, hi, ta, tb);
-        done = !(ta <= tb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = __int_as_float(__ldg(a.root + 1 + k));
+            hi[k] = __int_as_float(__ldg(a.root + 4 + k));
+        }
+        cta = tn;
+        ctb = tf;
+        slab(r, lo, hi, cta, ctb);
+        done = !(cta <= ctb);
+    }
+
+    __device__ __forceinline__ void pop()
+    {
+        if (sp == 0) {
+            done = true;
+        } else {
+            --sp;
+            ref = sref[sp];
+            cta = sta[sp];
+            ctb = stb[sp];
+        }
     }
 
     __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
@@ -411,48 +402,49 @@ template <int KIND, int STACK> struct TreeWalk {
             }
             if (ref < 0) {
                 if (-1 - (int64_t)ref < n_leaf) {
-                    float lo[3], hi[3];
-                    leaf_box_f(a, KIND, ref, lo, hi);
-                    ta = tn;
-                    tb = tf;
-                    slab(r, lo, hi, ta, tb);
-                    hit = ta <= tb;
+                    ta = cta;
+                    tb = ctb;
+                    hit = true;
+                    pop();
                 } else {
                     done = true;
                 }
-                if (sp == 0) done = true;
-                else ref = stack[--sp];
                 continue;
             }
             if (ref >= n_inner) {
                 done = true;
                 break;
             }
-            const uint4 *q = reinterpret_cast<const uint4 *>(a.nodes + ref);
-            uint4 q0 = __ldg(q), q1 = __ldg(q + 1);
-            // lbox = q0.x..q0.z (6 x u16), rbox = q0.w, q1.x, q1.y; left = q1.z, right = q1.w
-            float llo[3], lhi[3], rlo[3], rhi[3];
-            brick_box_f(a, q0.x & 0xffff, q0.x >> 16, q0.y & 0xffff, q0.y >> 16, q0.z & 0xffff,
-                        q0.z >> 16, llo, lhi);
-            brick_box_f(a, q0.w & 0xffff, q0.w >> 16, q1.x & 0xffff, q1.x >> 16, q1.y & 0xffff,
-                        q1.y >> 16, rlo, rhi);
+            const float4 *q = reinterpret_cast<const float4 *>(a.nodes + ref);
+            float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+            int4 q3 = __ldg(reinterpret_cast<const int4 *>(q + 3));
+            const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
+            const float rlo[3] = {q1.z, q1.w, q2.x}, rhi[3] = {q2.y, q2.z, q2.w};
             float la = tn, lb = tf, ra = tn, rb = tf;
             slab(r, llo, lhi, la, lb);
             slab(r, rlo, rhi, ra, rb);
             bool hl = la <= lb, hr = ra <= rb;
-            int32_t lc = (int32_t)q1.z, rc = (int32_t)q1.w;
             if (hl && hr) {
                 bool left_first = la <= ra;
-                if (sp < STACK) stack[sp++] = left_first ? rc : lc;
-                ref = left_first ? lc : rc;
+                if (sp < STACK) {
+                    sref[sp] = left_first ? q3.y : q3.x;
+                    sta[sp] = left_first ? ra : la;
+                    stb[sp] = left_first ? rb : lb;
+                    ++sp;
+                }
+                ref = left_first ? q3.x : q3.y;
+                cta = left_first ? la : ra;
+                ctb = left_first ? lb : rb;
             } else if (hl) {
-                ref = lc;
+                ref = q3.x;
+                cta = la;
+                ctb = lb;
             } else if (hr) {
-                ref = rc;
-            } else if (sp == 0) {
-                done = true;
+                ref = q3.y;
+                cta = ra;
+                ctb = rb;
             } else {
-                ref = stack[--sp];
+                pop();
             }
         }
         return hit;
@@ -598,7 +590,7 @@ __device__ __forceinline__ void count_samples(unsigned long long *samples, long 
 }
 
 template <typename T, int SAMPLER, int KIND>
-__global__ void __launch_bounds__(128) k_render(RArgs a, int tw)
+__global__ void __launch_bounds__(128, 8) k_render(RArgs a, int tw)
 {
     int x, y;
     block_pixel(tw, blockIdx.x, blockIdx.y, x, y);
@@ -616,7 +608,7 @@ struct BatchHeader {
 };
 
 template <typename T, int SAMPLER, int KIND>
-__global__ void __launch_bounds__(128) k_render_batch(const RArgs *__restrict__ items,
+__global__ void __launch_bounds__(128, 8) k_render_batch(const RArgs *__restrict__ items,
                                                       const int *__restrict__ tile_prefix,
                                                       BatchHeader *hdr)
 {
@@ -708,7 +700,6 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.nodes = j.st->nodes;
     a.root = j.st->root;
     a.count = j.st->kind == ESS_KD ? j.st->kd_count_dev : j.st->count;
-    a.kd_nodes = j.st->kd_nodes;
     a.samples = c.samples;
 }
 
