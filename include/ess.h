@@ -136,6 +136,12 @@ typedef struct {
                     (32 or 128 in the paper), 0 = none */
     int empty_test; /* 0 = brick min/max range test (Sec. 2, min-max range
                     queries), 1 = per-cell vote (Sec. 3.1 classifies per voxel) */
+    int rescan;  /* empty_test 0 only: 1 = recompute the per-brick min/max
+                    from the voxels in every build and rebuild (a full pass
+                    over the volume per TF edit, as when bricks are classified
+                    from their voxels after each edit, Sec. 3.1); 0 = compute
+                    it once per volume and brick size and reuse it (it does
+                    not depend on the TF).  Both give the same mask. */
 } ess_build_params;
 
 /* Builds a skipping structure of `kind` for volume `vol` under TF `tf`

@@ -155,9 +155,403 @@ __global__ void __launch_bounds__(256) k_brick_minmax(const T *__restrict__ vol,
     out[((size_t)bz * gy + by) * gx + bx] = make_float2(mn, mx);
 }
 
+// Vectorised form for rows made of whole 16-byte vectors and power-of-two
+// bricks.  One CTA per unit (brick row y, brick row z, chunk of 32 vectors in
+// x); lane l of each warp owns the 16-byte vector l of the chunk, i.e.
+// VPL = 16 / sizeof(T) consecutive voxel columns.  The unit's (B+2)^2 apron
+// rows are cut into steps of up to R consecutive rows of one z plane, dealt
+// round-robin to the CTA's warps; each warp keeps a few steps in flight with
+// cp.async copies (one coalesced 512-byte row per copy instruction) into a
+// per-warp ring in shared memory, and every lane reads back only the 16
+// bytes it copied itself.  Moving R rows per step spreads the pipeline's
+// bookkeeping (wait, commit, addressing) over R rows.  The brick region is a box,
+// so its minimum is the minimum over its x range of the per-column minima
+// over its rows: a lane accumulates column-wise minima/maxima (for 8-bit
+// voxels two columns per f16x2 register, one min/max instruction serving
+// both) and reduces across x once at the end, after the warps have
+// merged their columns through shared memory.  The apron columns on both
+// sides of a brick come from neighbouring lanes by shuffles; at a chunk
+// boundary the edge lane also copies the neighbouring chunk's vector.  With
+// B <= VPL a lane holds VPL / B whole bricks; with B > VPL a brick spans
+// B / VPL lanes, reduced by shuffles.
+
+// Two halves per register.  The f16x2 min/max is a single instruction; the
+// packed 16-bit integer forms measured several instructions each.
+__device__ __forceinline__ uint32_t min_h2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max_h2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Column-wise min/max over rows of one 16-byte vector per row (add), plus the
+// min/max of one edge column taken from another vector per row (edge: its
+// last voxel for the column left of the lane's vector, else its first).
+template <typename T> struct ColMinMax;
+template <> struct ColMinMax<uint8_t> {
+    // A byte b placed under the high byte 0x64 is the half 1024 + b, a normal
+    // f16 whose order is that of b: word i of the vector gives the half pairs
+    // (b0, b1) and (b2, b3), i.e. columns (4i, 4i+1) and (4i+2, 4i+3).
+    uint32_t mna[4], mnb[4], mxa[4], mxb[4];
+    uint32_t emn, emx;  // one edge column (see ColMinMax::edge)
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mna[i] = mnb[i] = 0x64ff64ffu, mxa[i] = mxb[i] = 0x64006400u;
+        emn = 0xffu, emx = 0u;
+    }
+    __device__ __forceinline__ void edge(const uint4 &w, bool last)
+    {
+        const uint32_t v = last ? w.w >> 24 : w.x & 0xffu;
+        emn = min(emn, v), emx = max(emx, v);
+    }
+    __device__ __forceinline__ float edge_min() const { return (float)emn; }
+    __device__ __forceinline__ float edge_max() const { return (float)emx; }
+    __device__ __forceinline__ void add(const uint4 &w)
+    {
+        const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t a = __byte_perm(q[i], 0x64646464u, 0x4140);
+            const uint32_t b = __byte_perm(q[i], 0x64646464u, 0x4342);
+            mna[i] = min_h2(mna[i], a);
+            mnb[i] = min_h2(mnb[i], b);
+            mxa[i] = max_h2(mxa[i], a);
+            mxb[i] = max_h2(mxb[i], b);
+        }
+    }
+    __device__ __forceinline__ void columns(float *mn, float *mx) const
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            mn[4 * i + 0] = (float)(mna[i] & 0xffu), mn[4 * i + 1] = (float)((mna[i] >> 16) & 0xffu);
+            mn[4 * i + 2] = (float)(mnb[i] & 0xffu), mn[4 * i + 3] = (float)((mnb[i] >> 16) & 0xffu);
+            mx[4 * i + 0] = (float)(mxa[i] & 0xffu), mx[4 * i + 1] = (float)((mxa[i] >> 16) & 0xffu);
+            mx[4 * i + 2] = (float)(mxb[i] & 0xffu), mx[4 * i + 3] = (float)((mxb[i] >> 16) & 0xffu);
+        }
+    }
+};
+template <> struct ColMinMax<uint16_t> {
+    uint32_t mn[8], mx[8];  // column j of the vector
+    uint32_t emn, emx;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mn[j] = 0xffffu, mx[j] = 0u;
+        emn = 0xffffu, emx = 0u;
+    }
+    __device__ __forceinline__ void edge(const uint4 &w, bool last)
+    {
+        const uint32_t v = last ? w.w >> 16 : w.x & 0xffffu;
+        emn = min(emn, v), emx = max(emx, v);
+    }
+    __device__ __forceinline__ float edge_min() const { return (float)emn; }
+    __device__ __forceinline__ float edge_max() const { return (float)emx; }
+    __device__ __forceinline__ void add(const uint4 &w)
+    {
+        const uint32_t q[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t lo = q[i] & 0xffffu, hi = q[i] >> 16;
+            mn[2 * i] = min(mn[2 * i], lo), mx[2 * i] = max(mx[2 * i], lo);
+            mn[2 * i + 1] = min(mn[2 * i + 1], hi), mx[2 * i + 1] = max(mx[2 * i + 1], hi);
+        }
+    }
+    __device__ __forceinline__ void columns(float *cmn, float *cmx) const
+    {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cmn[j] = (float)mn[j], cmx[j] = (float)mx[j];
+    }
+};
+template <> struct ColMinMax<float> {
+    float mnf[4], mxf[4];
+    float emn, emx;
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mnf[i] = INFINITY, mxf[i] = -INFINITY;
+        emn = INFINITY, emx = -INFINITY;
+    }
+    __device__ __forceinline__ void edge(const uint4 &w, bool last)
+    {
+        const float v = __uint_as_float(last ? w.w : w.x);
+        emn = fminf(v, emn), emx = fmaxf(v, emx);
+    }
+    __device__ __forceinline__ float edge_min() const { return emn; }
+    __device__ __forceinline__ float edge_max() const { return emx; }
+    __device__ __forceinline__ void add(const uint4 &w)
+    {
+        const float q[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z),
+                            __uint_as_float(w.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            mnf[i] = fminf(q[i], mnf[i]);
+            mxf[i] = fmaxf(q[i], mxf[i]);
+        }
+    }
+    __device__ __forceinline__ void columns(float *mn, float *mx) const
+    {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mn[i] = mnf[i], mx[i] = mxf[i];
+    }
+};
+
+constexpr int MM_WARPS = 2;  // warps per unit
+constexpr int MM_SLOT = 34;  // 16-byte vectors per row slot: 32 lanes + 2 edge vectors
+
+// Pipeline shape for brick size B: a step moves a block of R consecutive
+// rows of one z plane, NB blocks cover the plane's B + 2 apron rows, and a
+// warp keeps DEPTH steps (about 20 rows) in flight.  Interior units have an
+// even number B + 2 of planes, so the two warps get equal shares.
+template <int B> struct MmShape {
+    static constexpr int NB = (B + 2 + 9) / 10;
+    static constexpr int R = (B + 2 + NB - 1) / NB;
+    static constexpr int DEPTH = 20 / R > 2 ? 20 / R : 2;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ uint4 lds16(uint32_t smem)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(smem)
+                 : "memory");
+    return v;
+}
+template <typename T, int B>
+__global__ void __launch_bounds__(MM_WARPS * 32) k_brick_minmax_vec(const T *__restrict__ vol, int nx,
+                                                                    int ny, int nz, int gx, int gy,
+                                                                    int gz, float2 *__restrict__ out)
+{
+    constexpr int VPL = 16 / (int)sizeof(T);
+    constexpr int R = MmShape<B>::R, NB = MmShape<B>::NB, DEPTH = MmShape<B>::DEPTH;
+    constexpr int NCOL = 2 * VPL + 2;  // merged floats per lane: columns min/max, edge min/max
+    constexpr int ROW_BYTES = MM_SLOT * 16;
+    constexpr int STEP_BYTES = R * ROW_BYTES;
+    constexpr int RING_BYTES = DEPTH * STEP_BYTES;
+    constexpr int MERGE_BYTES = NCOL * 32 * 4;
+    constexpr int WARP_BYTES = RING_BYTES > MERGE_BYTES ? RING_BYTES : MERGE_BYTES;
+    static_assert(NB * R >= B + 2, "blocks must cover the apron rows");
+    __shared__ __align__(16) unsigned char smem[MM_WARPS * WARP_BYTES];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row_vecs = nx / VPL;
+    const int nchunk = (row_vecs + 31) >> 5;
+    const int chunk = blockIdx.x % nchunk;
+    const int rest = blockIdx.x / nchunk;
+    const int by = rest % gy, bz = rest / gy;
+    const int vec = chunk * 32 + lane;
+    const bool have = vec < row_vecs;
+    const bool ledge = lane == 0 && chunk > 0;             // column x0 - 1 is another chunk's
+    const bool redge = lane == 31 && vec + 1 < row_vecs;  // column x0 + VPL is another chunk's
+    const bool edge = ledge || redge;
+    const bool edges = nchunk > 1;  // uniform: some lane of the unit needs an edge column
+    const int y0 = max(by * B - 1, 0), y1 = min((by + 1) * B, ny - 1);
+    const int z0 = max(bz * B - 1, 0), z1 = min((bz + 1) * B, nz - 1);
+    const int nyr = y1 - y0 + 1;
+    // steps g = (plane g / NB, block g % NB), dealt round-robin to the warps
+    const int nsteps = (z1 - z0 + 1) * NB;
+    const int my_steps = nsteps > wid ? (nsteps - wid + MM_WARPS - 1) / MM_WARPS : 0;
+
+    // shared addresses of the lane's vector and of its edge vector in row 0 of slot 0
+    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(smem + wid * WARP_BYTES);
+    const uint32_t mine = ring + lane * 16, edge_at = ring + (ledge ? 32 : 33) * 16;
+    const size_t rv = (size_t)row_vecs;
+    // A lane past the row's end copies the row's last vector: its columns are
+    // then copies of voxels that the last brick holds anyway.
+    const uint4 *base = reinterpret_cast<const uint4 *>(vol) + min(vec, row_vecs - 1);
+    const int edelta = ledge ? -1 : 1;
+    auto rows_of = [&](int k) {  // valid rows of this warp's step k
+        const int blk = (wid + MM_WARPS * k) % NB;
+        return min(R, nyr - blk * R);
+    };
+    auto issue = [&](int k, uint32_t off) {
+        if (k < my_steps) {
+            const int g = wid + MM_WARPS * k;
+            const int blk = g % NB;
+            const int nv = min(R, nyr - blk * R);
+            const uint4 *src = base + ((size_t)(z0 + g / NB) * ny + (y0 + blk * R)) * rv;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if (j < nv) {
+                    cp_async16(mine + off + j * ROW_BYTES, src + j * rv);
+                    if (edge) cp_async16(edge_at + off + j * ROW_BYTES, src + j * rv + edelta);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < DEPTH; ++k) issue(k, k * STEP_BYTES);
+
+    ColMinMax<T> acc;
+    acc.init();
+    uint32_t off = 0;
+    for (int k = 0; k < my_steps; ++k) {
+        cp_async_wait<DEPTH - 1>();  // step k has landed
+        const int nv = rows_of(k);
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            if (j < nv) {
+                acc.add(lds16(mine + off + j * ROW_BYTES));
+                // lanes without an edge column read a slot nobody wrote and
+                // discard the result; no branch on the lane
+                if (edges) acc.edge(lds16(edge_at + off + j * ROW_BYTES), ledge);
+            }
+        }
+        issue(k + DEPTH, off);
+        off = off + STEP_BYTES == RING_BYTES ? 0u : off + STEP_BYTES;
+    }
+    cp_async_wait<0>();
+    const float emn = acc.edge_min(), emx = acc.edge_max();  // meaningful on edge lanes only
+
+    // merge the warps' columns through shared memory (the rings are done)
+    float cmn[VPL], cmx[VPL];
+    acc.columns(cmn, cmx);
+    float lmn = emn, lmx = emx;
+    __syncthreads();
+    float *mrg = reinterpret_cast<float *>(smem);
+    if (wid > 0) {
+        float *m = reinterpret_cast<float *>(smem + wid * WARP_BYTES);
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) m[j * 32 + lane] = cmn[j], m[(VPL + j) * 32 + lane] = cmx[j];
+        m[(2 * VPL) * 32 + lane] = lmn;
+        m[(2 * VPL + 1) * 32 + lane] = lmx;
+    }
+    __syncthreads();
+    if (wid > 0) return;
+#pragma unroll
+    for (int w = 1; w < MM_WARPS; ++w) {
+        const float *m = mrg + w * (WARP_BYTES / 4);
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) {
+            const float a = m[j * 32 + lane], b = m[(VPL + j) * 32 + lane];
+            cmn[j] = a < cmn[j] ? a : cmn[j];
+            cmx[j] = b > cmx[j] ? b : cmx[j];
+        }
+        const float a0 = m[(2 * VPL) * 32 + lane], a1 = m[(2 * VPL + 1) * 32 + lane];
+        lmn = fminf(a0, lmn);
+        lmx = fmaxf(a1, lmx);
+    }
+
+    // apron columns left and right of the lane's VPL columns
+    float amn = __shfl_up_sync(0xffffffffu, cmn[VPL - 1], 1);
+    float amx = __shfl_up_sync(0xffffffffu, cmx[VPL - 1], 1);
+    float bmn = __shfl_down_sync(0xffffffffu, cmn[0], 1);
+    float bmx = __shfl_down_sync(0xffffffffu, cmx[0], 1);
+    if (lane == 0) {
+        amn = ledge ? lmn : cmn[0];  // x = 0 clamps to itself
+        amx = ledge ? lmx : cmx[0];
+    }
+    if (vec + 1 >= row_vecs) {
+        bmn = cmn[VPL - 1];  // x = nx - 1 clamps to itself
+        bmx = cmx[VPL - 1];
+    } else if (lane == 31) {
+        bmn = lmn;
+        bmx = lmx;
+    }
+    if constexpr (B <= VPL) {
+        constexpr int PER = VPL / B;
+        if (!have) return;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            float m0 = k == 0 ? amn : cmn[k * B - 1];
+            float m1 = k == 0 ? amx : cmx[k * B - 1];
+            const float e0 = k == PER - 1 ? bmn : cmn[(k + 1) * B];
+            const float e1 = k == PER - 1 ? bmx : cmx[(k + 1) * B];
+            m0 = e0 < m0 ? e0 : m0;
+            m1 = e1 > m1 ? e1 : m1;
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                m0 = cmn[k * B + j] < m0 ? cmn[k * B + j] : m0;
+                m1 = cmx[k * B + j] > m1 ? cmx[k * B + j] : m1;
+            }
+            out[((size_t)bz * gy + by) * gx + vec * PER + k] = make_float2(m0, m1);
+        }
+    } else {
+        constexpr int LANES = B / VPL;  // divides 32
+        float m0 = cmn[0], m1 = cmx[0];
+#pragma unroll
+        for (int j = 1; j < VPL; ++j) {
+            m0 = cmn[j] < m0 ? cmn[j] : m0;
+            m1 = cmx[j] > m1 ? cmx[j] : m1;
+        }
+        if (vec % LANES == 0) {
+            m0 = amn < m0 ? amn : m0;
+            m1 = amx > m1 ? amx : m1;
+        }
+        if (vec % LANES == LANES - 1 || vec + 1 >= row_vecs) {
+            m0 = bmn < m0 ? bmn : m0;
+            m1 = bmx > m1 ? bmx : m1;
+        }
+#pragma unroll
+        for (int o = 1; o < LANES; o <<= 1) {
+            const float a0 = __shfl_xor_sync(0xffffffffu, m0, o);
+            const float a1 = __shfl_xor_sync(0xffffffffu, m1, o);
+            m0 = a0 < m0 ? a0 : m0;
+            m1 = a1 > m1 ? a1 : m1;
+        }
+        if (have && vec % LANES == 0) out[((size_t)bz * gy + by) * gx + vec / LANES] = make_float2(m0, m1);
+    }
+}
+
+template <typename T>
+bool launch_minmax_vec(Ctx &c, const T *data, int nx, int ny, int nz, int B, int gx, int gy, int gz,
+                       float2 *out)
+{
+    constexpr int VPL = 16 / (int)sizeof(T);
+    if ((nx % VPL) != 0 || ((uintptr_t)data & 15u) != 0) return false;
+    size_t units = (size_t)((nx / VPL + 31) / 32) * gy * gz;
+    if (units > (size_t)INT32_MAX) return false;
+    unsigned blocks = (unsigned)units;
+    Launch L(c, "brick_minmax");
+#define ESS_MMV(BB)                                                                           \
+    case BB:                                                                                  \
+        k_brick_minmax_vec<T, BB>                                                             \
+            <<<blocks, MM_WARPS * 32, 0, c.stream>>>(data, nx, ny, nz, gx, gy, gz, out);      \
+        return true;
+    switch (B) {
+        ESS_MMV(2)
+        ESS_MMV(4)
+        ESS_MMV(8)
+        ESS_MMV(16)
+        ESS_MMV(32)
+        ESS_MMV(64)
+    }
+#undef ESS_MMV
+    return false;
+}
+
 void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out)
 {
     int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
+    bool done = false;
+    switch (v.dtype) {
+    case ESS_U8:
+        done = launch_minmax_vec(c, (const uint8_t *)v.data, v.nx, v.ny, v.nz, B, gx, gy, gz, out);
+        break;
+    case ESS_U16:
+        done = launch_minmax_vec(c, (const uint16_t *)v.data, v.nx, v.ny, v.nz, B, gx, gy, gz, out);
+        break;
+    default:
+        done = launch_minmax_vec(c, (const float *)v.data, v.nx, v.ny, v.nz, B, gx, gy, gz, out);
+    }
+    if (done) return;
+    // any other row length or brick size: one thread per brick
     size_t warps = (size_t)((gx + 31) / 32) * gy * gz;
     unsigned blocks = (unsigned)((warps + 7) / 8);
     Launch L(c, "brick_minmax");

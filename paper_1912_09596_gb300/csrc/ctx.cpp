@@ -204,10 +204,15 @@ void set_sampler(Ctx &c, Volume &v, int mode)
     }
 }
 
-float2 *minmax_for(Ctx &c, Volume &v, int B)
+// Per-brick min/max of volume v for brick size B, computed on first use and
+// kept with the volume; `rescan` recomputes a kept one.
+float2 *minmax_for(Ctx &c, Volume &v, int B, bool rescan)
 {
     auto it = v.minmax.find(B);
-    if (it != v.minmax.end()) return it->second;
+    if (it != v.minmax.end()) {
+        if (rescan) launch_brick_minmax(c, v, B, it->second);
+        return it->second;
+    }
     int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
     float2 *mm = (float2 *)c.alloc(sizeof(float2) * (size_t)gx * gy * gz);
     launch_brick_minmax(c, v, B, mm);
@@ -277,7 +282,7 @@ void run_build(Ctx &c, Structure &s)
     if (s.p.empty_test == 1) {
         launch_brick_mask_cells(c, v, B, t, sc, s.mask, s.gx, s.gy, s.gz);
     } else {
-        float2 *mm = minmax_for(c, v, B);
+        float2 *mm = minmax_for(c, v, B, s.p.rescan == 1);
         launch_brick_mask(c, mm, s.nb, t, v.value_lo, sc, s.mask);
     }
     launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums,
@@ -544,7 +549,7 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         TF &t = get_tf(c, tf);
         ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_KD || kind == ESS_NONE,
                     "unknown structure kind");
-        ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0};
+        ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0, 0};
         auto s = std::make_unique<Structure>();
         s->kind = kind;
         s->vol = vol;
@@ -556,6 +561,7 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
             ESS_REQUIRE(p.halting == 0 || p.halting == 1, "halting must be 0 or 1");
             ESS_REQUIRE(p.mls >= 0, "mls must be >= 0");
             ESS_REQUIRE(p.empty_test == 0 || p.empty_test == 1, "empty_test must be 0 or 1");
+            ESS_REQUIRE(p.rescan == 0 || p.rescan == 1, "rescan must be 0 or 1");
             int B = p.brick;
             s->gx = (v.nx + B - 1) / B;
             s->gy = (v.ny + B - 1) / B;
@@ -652,7 +658,7 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
         case ESS_ARR_MINMAX: {
             ESS_REQUIRE(s.p.empty_test == 0, "min/max is only kept for the range test");
             Volume &v = get_vol(c, s.vol);
-            copy_out(c, dst, minmax_for(c, v, s.p.brick), sizeof(float2) * s.nb, capacity, written);
+            copy_out(c, dst, minmax_for(c, v, s.p.brick, false), sizeof(float2) * s.nb, capacity, written);
             break;
         }
         case ESS_ARR_MASK: copy_out(c, dst, s.mask, (size_t)s.nb, capacity, written); break;
@@ -838,7 +844,7 @@ ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_c
         std::string err;
         for (int kind : kinds) {
             for (int B : bricks) {
-                ess_build_params bp{B, 4, 1, 32, 0};
+                ess_build_params bp{B, 4, 1, 32, 0, 0};
                 ess_handle h = 0;
                 if (ess_build(ctx, vol, tf, (ess_kind)kind, &bp, &h) != ESS_OK) {
                     c.last_error.clear();

@@ -40,7 +40,7 @@ class EssError(RuntimeError):
 
 class BuildParams(C.Structure):
     _fields_ = [("brick", C.c_int), ("nbins", C.c_int), ("halting", C.c_int),
-                ("mls", C.c_int), ("empty_test", C.c_int)]
+                ("mls", C.c_int), ("empty_test", C.c_int), ("rescan", C.c_int)]
 
 
 class Camera(C.Structure):
@@ -215,8 +215,8 @@ def ess_tf_update(ctx, tf, rgba):
     _check(ctx, lib.ess_tf_update(ctx, tf, p, dev, int(rgba.shape[0])))
 
 
-def build_params(brick=8, nbins=4, halting=1, mls=0, empty_test=0):
-    return BuildParams(brick, nbins, halting, mls, empty_test)
+def build_params(brick=8, nbins=4, halting=1, mls=0, empty_test=0, rescan=0):
+    return BuildParams(brick, nbins, halting, mls, empty_test, rescan)
 
 
 def ess_build(ctx, vol, tf, kind, params=None):

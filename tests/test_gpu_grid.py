@@ -49,6 +49,39 @@ def test_minmax_mask_ids_bit_exact(gpu, ctx, ora, case, B):
         ess.ess_release(ctx, st)
 
 
+def _row_volumes():
+    """Rows of whole 16-byte vectors, more than 32 vectors per row (two warps
+    share a brick row) and, for the wide bricks, a ragged last brick in x."""
+    rng = np.random.default_rng(21)
+    yield "u8_528", rng.integers(0, 256, (19, 21, 528)).astype(np.uint8), (0, 255)
+    yield "u16_264", rng.integers(0, 65536, (17, 23, 264)).astype(np.uint16), (0, 65535)
+    yield "f32_136", rng.uniform(-3, 5, (18, 13, 136)).astype(np.float32), (-3.0, 5.0)
+    yield "u8_64", synth.blobs_u8((9, 70, 64), n_blobs=5, seed=3), (0, 255)
+
+
+@pytest.mark.parametrize("case", list(_row_volumes()), ids=lambda c: c[0])
+@pytest.mark.parametrize("B", [2, 4, 8, 16, 32, 64, 6])
+def test_minmax_vector_rows_and_rescan(gpu, ctx, ora, case, B):
+    """The per-brick min/max over whole-vector rows, for every brick size
+    (powers of two take the vectorised reduction, 6 the per-brick one), equals
+    the oracle bit for bit, and recomputing it in every rebuild (rescan)
+    gives the same min/max and mask."""
+    ess, torch = gpu
+    name, v, (lo, hi) = case
+    tf = synth.tf_random_sparse(256, seed=B, p_zero=0.6)
+    vol, t = upload(ess, torch, ctx, v, lo, hi, tf)
+    ov, ot = ora.OVolume(v, lo, hi), ora.OTF(tf)
+    rmin, rmax = ora.brick_minmax(ov, B)
+    ref = ora.brick_mask(rmin, rmax, ot, lo, hi)
+    for rescan in (1, 0, 1):
+        st = ess.ess_build(ctx, vol, t, ess.GRID, ess.build_params(brick=B, rescan=rescan))
+        ess.ess_rebuild(ctx, st)
+        mm = ess.ess_structure_read(ctx, st, ess.ARR_MINMAX).reshape(-1, 2)
+        assert np.array_equal(bits(mm[:, 0]), bits(rmin)) and np.array_equal(bits(mm[:, 1]), bits(rmax))
+        assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_MASK), ref)
+        ess.ess_release(ctx, st)
+
+
 @pytest.mark.parametrize("case", VOLS, ids=lambda c: c[0])
 @pytest.mark.parametrize("ert", [2.0, 0.95])
 def test_render_naive_and_grid_match_oracle(gpu, ctx, ora, case, ert):
