@@ -172,12 +172,14 @@ void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
         ESS_CUDA(cudaMemcpyAsync(t.table, rgba, bytes, cudaMemcpyDeviceToDevice, c.stream));
     } else {
         check_tf_host(rgba, t.nt);
-        if (!t.staging) ESS_CUDA(cudaMallocHost(&t.staging, bytes));
-        if (t.staged) ESS_CUDA(cudaEventSynchronize(t.staged));
-        std::memcpy(t.staging, rgba, bytes);
-        ESS_CUDA(cudaMemcpyAsync(t.table, t.staging, bytes, cudaMemcpyHostToDevice, c.stream));
-        if (!t.staged) ESS_CUDA(cudaEventCreateWithFlags(&t.staged, cudaEventDisableTiming));
-        ESS_CUDA(cudaEventRecord(t.staged, c.stream));
+        const int k = t.stage_next;
+        if (!t.staging[k]) ESS_CUDA(cudaMallocHost(&t.staging[k], bytes));
+        if (t.staged[k]) ESS_CUDA(cudaEventSynchronize(t.staged[k]));
+        std::memcpy(t.staging[k], rgba, bytes);
+        ESS_CUDA(cudaMemcpyAsync(t.table, t.staging[k], bytes, cudaMemcpyHostToDevice, c.stream));
+        if (!t.staged[k]) ESS_CUDA(cudaEventCreateWithFlags(&t.staged[k], cudaEventDisableTiming));
+        ESS_CUDA(cudaEventRecord(t.staged[k], c.stream));
+        t.stage_next = (k + 1) % STAGE_RING;
     }
     // entry nt repeats entry nt-1 so that the renderer's upper neighbour needs no clamp
     ESS_CUDA(cudaMemcpyAsync(t.table + t.nt, t.table + (t.nt - 1), sizeof(float4),
@@ -379,8 +381,10 @@ ess_status ess_destroy(ess_ctx *ctx)
         c.free(c.stage);
         ESS_CUDA(cudaStreamSynchronize(c.stream));
         for (auto &kv : c.tfs) {
-            if (kv.second->staging) cudaFreeHost(kv.second->staging);
-            if (kv.second->staged) cudaEventDestroy(kv.second->staged);
+            for (int k = 0; k < STAGE_RING; ++k) {
+                if (kv.second->staging[k]) cudaFreeHost(kv.second->staging[k]);
+                if (kv.second->staged[k]) cudaEventDestroy(kv.second->staged[k]);
+            }
         }
         for (auto &p : c.pending) {
             cudaEventDestroy(p.a);
@@ -391,8 +395,10 @@ ess_status ess_destroy(ess_ctx *ctx)
             Ctx::BatchGroup &g = kv.second;
             if (g.exec) cudaGraphExecDestroy(g.exec);
             if (g.graph) cudaGraphDestroy(g.graph);
-            if (g.done) cudaEventDestroy(g.done);
-            if (g.host) cudaFreeHost(g.host);
+            for (int k = 0; k < STAGE_RING; ++k) {
+                if (g.done[k]) cudaEventDestroy(g.done[k]);
+                if (g.host[k]) cudaFreeHost(g.host[k]);
+            }
             if (g.dev) cudaFree(g.dev);
         }
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
@@ -443,8 +449,10 @@ ess_status ess_release(ess_ctx *ctx, ess_handle h)
             c.free(t.table);
             c.free(t.prefix);
             ESS_CUDA(cudaStreamSynchronize(c.stream));
-            if (t.staging) cudaFreeHost(t.staging);
-            if (t.staged) cudaEventDestroy(t.staged);
+            for (int k = 0; k < STAGE_RING; ++k) {
+                if (t.staging[k]) cudaFreeHost(t.staging[k]);
+                if (t.staged[k]) cudaEventDestroy(t.staged[k]);
+            }
             c.tfs.erase(h);
         } else {
             throw Error{ESS_ERR_HANDLE, "unknown handle"};
@@ -768,22 +776,25 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
             Ctx::BatchGroup &g = c.batch[kv.first];
             std::vector<RenderJob> &jobs = kv.second;
             int n = (int)jobs.size();
-            if (!g.host) {
+            if (!g.dev) {
                 g.cap = batch_bytes(BATCH_MAX);
-                ESS_CUDA(cudaMallocHost(&g.host, g.cap));
                 ESS_CUDA(cudaMalloc(&g.dev, g.cap));
-                ESS_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
-                ESS_CUDA(cudaEventRecord(g.done, c.stream));
             }
-            // the previous replay of this group must have read the staging
-            ESS_CUDA(cudaEventSynchronize(g.done));
-            size_t bytes = pack_batch(c, jobs.data(), n, tw, g.host, g.cap);
+            const int k = g.next;
+            if (!g.host[k]) {
+                ESS_CUDA(cudaMallocHost(&g.host[k], g.cap));
+                ESS_CUDA(cudaEventCreateWithFlags(&g.done[k], cudaEventDisableTiming));
+                ESS_CUDA(cudaEventRecord(g.done[k], c.stream));
+            }
+            // the replay that last read this slot must have run
+            ESS_CUDA(cudaEventSynchronize(g.done[k]));
+            size_t bytes = pack_batch(c, jobs.data(), n, tw, g.host[k], g.cap);
             if (!g.exec) {
                 // capture: copy of the packed batch + the persistent kernel
                 ESS_CUDA(cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal));
                 cudaStream_t saved = c.stream;
                 c.stream = c.capture_stream;
-                cudaError_t e1 = cudaMemcpyAsync(g.dev, g.host, bytes, cudaMemcpyHostToDevice, c.stream);
+                cudaError_t e1 = cudaMemcpyAsync(g.dev, g.host[k], bytes, cudaMemcpyHostToDevice, c.stream);
                 try {
                     if (e1 == cudaSuccess)
                         launch_render_batch(c, jobs[0].st->kind, jobs[0].vol->dtype,
@@ -810,14 +821,15 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
                 ESS_REQUIRE(g.copy_node, "internal: batch graph has no copy node");
                 ESS_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
             } else {
-                ESS_CUDA(cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.copy_node, g.dev, g.host, bytes,
-                                                            cudaMemcpyHostToDevice));
+                ESS_CUDA(cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.copy_node, g.dev, g.host[k],
+                                                            bytes, cudaMemcpyHostToDevice));
             }
             {
                 Launch L(c, "render_batch");
                 ESS_CUDA(cudaGraphLaunch(g.exec, c.stream));
             }
-            ESS_CUDA(cudaEventRecord(g.done, c.stream));
+            ESS_CUDA(cudaEventRecord(g.done[k], c.stream));
+            g.next = (k + 1) % STAGE_RING;
         }
     });
 }

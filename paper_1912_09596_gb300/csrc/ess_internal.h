@@ -74,13 +74,20 @@ struct Volume {
     bool released = false;
 };
 
+// Pinned staging slots per TF and per batch group: the host fills the next
+// slot while earlier uploads may still be queued behind running kernels.
+constexpr int STAGE_RING = 4;
+
 struct TF {
     int nt;
     float4 *table = nullptr;  // device, nt entries
     int *prefix = nullptr;    // device, nt+1 counts of alpha > 0
     uint64_t version = 0;     // bumped by every update
-    float *staging = nullptr;       // pinned host copy for asynchronous uploads
-    cudaEvent_t staged = nullptr;   // completion of the last staged upload
+    // pinned host copies for asynchronous uploads, used in turn; a slot is
+    // rewritten only after the upload that last read it has run
+    float *staging[STAGE_RING] = {};
+    cudaEvent_t staged[STAGE_RING] = {};
+    int stage_next = 0;
     int refs = 0;
     bool released = false;
 };
@@ -161,13 +168,14 @@ struct Ctx {
     std::map<std::string, std::pair<uint64_t, double>> prof;
     // batched rendering: one captured graph per (dtype, kind) group
     struct BatchGroup {
-        void *host = nullptr;       // pinned staging
-        void *dev = nullptr;        // device copy
+        void *host[STAGE_RING] = {};        // pinned staging slots, used in turn
+        cudaEvent_t done[STAGE_RING] = {};  // the replay that last read each slot has run
+        int next = 0;
+        void *dev = nullptr;  // device copy (replays are ordered on the stream)
         size_t cap = 0;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         cudaGraphNode_t copy_node = nullptr;
-        cudaEvent_t done = nullptr;  // last replay finished reading the staging
         int n_captured = -1;
     };
     std::map<int, BatchGroup> batch;

@@ -22,6 +22,8 @@
 // kernel emits them.  With an even nbins the middle plane lo + floor(e/2) is
 // candidate j = nbins/2, so a forced middle split also falls on a slab border.
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 #include <limits.h>
 #include <stdint.h>
 
@@ -667,10 +669,15 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
 
 // Whether the whole build runs as one device-driven graph: binned planes and
 // level buffers for the widest possible level (one node per non-empty brick)
-// within an eighth of the free memory.
+// within an eighth of the free memory.  The environment variable
+// ESS_KD_GRAPH=0 selects the host-driven level loop instead (same kernels,
+// same tree): profilers that time kernels one by one cannot look inside a
+// graph with a conditional node.
 static bool kd_graph_fits(const Structure &s, int S)
 {
     if (s.p.nbins == 0) return false;
+    const char *env = std::getenv("ESS_KD_GRAPH");
+    if (env && env[0] == '0') return false;
     size_t cap = (size_t)s.nb;
     size_t bytes = 2 * cap * 3 * S * 6 * sizeof(int32_t) + cap * 3 * S * sizeof(unsigned long long) +
                    cap * sizeof(KdDecision) + ((cap + 255) / 256) * sizeof(uint32_t);

@@ -46,6 +46,8 @@ struct RArgs {
 struct Ray {
     float o[3], d[3], inv[3];
     bool zero[3];
+    // box-tree slab tests: a finite inverse (1e30 on zero axes) and -o * sinv
+    float sinv[3], noi[3];
 };
 
 struct Acc {
@@ -74,6 +76,8 @@ __device__ __forceinline__ void gen_ray(const RArgs &a, int x, int y, Ray &r)
         r.d[i] = dir[i] / len;
         r.zero[i] = !(fabsf(r.d[i]) >= 1e-30f);
         r.inv[i] = r.zero[i] ? 0.0f : 1.0f / r.d[i];
+        r.sinv[i] = r.zero[i] ? 1e30f : r.inv[i];
+        r.noi[i] = -(r.o[i] * r.sinv[i]);
     }
 }
 
@@ -96,6 +100,42 @@ __device__ __forceinline__ void slab(const Ray &r, const float lo[3], const floa
         if (tn > tmin) tmin = tn;
         if (tx < tmax) tmax = tx;
     }
+}
+
+__device__ __forceinline__ float fmax3f(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float fmin3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Slab test of the box-tree traversals: plane crossings as fmaf(p, sinv,
+// -o * sinv), branch-free (a zero axis has the finite inverse 1e30, so a box
+// keeps the ray iff its slab contains o, up to one rounding of o * 1e30 that
+// two boxes sharing the plane see alike, so at least one of them keeps it).
+// It may differ from the exact test by rounding; a crossing misplaced along
+// an axis moves the ray's position by a tiny fraction of a voxel, which the
+// one-voxel apron of the brick min/max absorbs (a sample just outside a box
+// reads only voxels that the box's range test covered), and rule S adds a
+// sample at both ends of every interval.
+__device__ __forceinline__ void slab_tree(const Ray &r, const float lo[3], const float hi[3],
+                                          float &tmin, float &tmax)
+{
+    float n[3], f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float t0 = fmaf(lo[a], r.sinv[a], r.noi[a]), t1 = fmaf(hi[a], r.sinv[a], r.noi[a]);
+        n[a] = fminf(t0, t1);
+        f[a] = fmaxf(t0, t1);
+    }
+    tmin = fmax3f(n[0], n[1], fmaxf(n[2], tmin));
+    tmax = fmin3f(f[0], f[1], fminf(f[2], tmax));
 }
 
 // -------------------------------------------------------- sampling (R2, R5)
@@ -140,10 +180,11 @@ template <> struct Corners<uint8_t, 1> {
     static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
     {
         uint2 c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_index(a, ix, iy, iz));
+        // byte b under the exponent of 2^23 is the float 2^23 + b: exact
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[k] = (float)((c.x >> (8 * k)) & 0xffu);
-            v[4 + k] = (float)((c.y >> (8 * k)) & 0xffu);
+            v[k] = __int_as_float(__byte_perm(c.x, 0x4b000000u, 0x7650 | k)) - 8388608.0f;
+            v[4 + k] = __int_as_float(__byte_perm(c.y, 0x4b000000u, 0x7650 | k)) - 8388608.0f;
         }
     }
 };
@@ -155,8 +196,8 @@ template <> struct Corners<uint16_t, 1> {
         uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            v[2 * k] = (float)(w[k] & 0xffffu);
-            v[2 * k + 1] = (float)(w[k] >> 16);
+            v[2 * k] = __int_as_float(__byte_perm(w[k], 0x4b000000u, 0x7610)) - 8388608.0f;
+            v[2 * k + 1] = __int_as_float(__byte_perm(w[k], 0x4b000000u, 0x7632)) - 8388608.0f;
         }
     }
 };
@@ -191,8 +232,7 @@ __device__ __forceinline__ float4 classify(const RArgs &a, float v)
 {
     float x = (v - a.value_lo) * a.s;
     float xmax = (float)(a.nt - 1);
-    x = x < 0.0f ? 0.0f : x;
-    x = x > xmax ? xmax : x;
+    x = fminf(fmaxf(x, 0.0f), xmax);  // x is finite
     int i0 = (int)x;
     float w = x - (float)i0;
     float4 c0 = __ldg(a.tf + i0), c1 = __ldg(a.tf + i0 + 1);
@@ -214,33 +254,10 @@ __device__ __forceinline__ bool sample_step(const RArgs &a, const Ray &r, float 
     return acc.a >= a.ert;
 }
 
-// Rule S over one hit interval; returns true when the ray is finished.  The
-// loop counter is kept as a float as well (exact below 2^24), which is the
-// value (float)k.
-template <typename T, int SAMPLER>
-__device__ __forceinline__ bool march(const RArgs &a, const Ray &r, float tn, float tf, float ta,
-                                      float tb, int &k_next, Acc &acc, long long &ns)
-{
-    float ka = ceilf((ta - tn) / a.dt) - 1.0f;
-    float kb = floorf((tb - tn) / a.dt) + 1.0f;
-    kb = kb < 16777216.0f ? kb : 16777216.0f;
-    int k0 = ka > (float)k_next ? (int)ka : k_next;
-    int k1 = (int)kb;
-    float kf = (float)k0;
-    for (int k = k0; k <= k1; ++k, kf += 1.0f) {
-        float t = fmaf(kf, a.dt, tn);
-        if (!(t < tf)) return true;
-        ++ns;
-        if (sample_step<T, SAMPLER>(a, r, t, acc)) return true;
-    }
-    if (k1 + 1 > k_next) k_next = k1 + 1;
-    return false;
-}
-
 // ------------------------------------------------------------- traversals
 template <typename T, int SAMPLER>
 __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float tn, float tf,
-                                            Acc &acc, long long &ns)
+                                            Acc &acc, int &ns)
 {
     float kf = 0.0f;
     for (int k = 0; k < 16777216; ++k, kf += 1.0f) {
@@ -349,8 +366,7 @@ struct GridWalk {
 // Reference and iteration bounds keep a corrupt structure from reading
 // outside its buffers or looping; a valid tree never reaches them.
 template <int KIND, int STACK> struct TreeWalk {
-    int32_t sref[STACK];
-    float sta[STACK], stb[STACK];
+    float4 stk[STACK];  // pushed (ref bits, ta, tb, unused): one 16-byte store/load
     int sp, budget, n_inner;
     int64_t n_leaf;
     int32_t ref;
@@ -375,7 +391,7 @@ template <int KIND, int STACK> struct TreeWalk {
         }
         cta = tn;
         ctb = tf;
-        slab(r, lo, hi, cta, ctb);
+        slab_tree(r, lo, hi, cta, ctb);
         done = !(cta <= ctb);
     }
 
@@ -385,9 +401,10 @@ template <int KIND, int STACK> struct TreeWalk {
             done = true;
         } else {
             --sp;
-            ref = sref[sp];
-            cta = sta[sp];
-            ctb = stb[sp];
+            const float4 e = stk[sp];
+            ref = __float_as_int(e.x);
+            cta = e.y;
+            ctb = e.z;
         }
     }
 
@@ -421,15 +438,14 @@ template <int KIND, int STACK> struct TreeWalk {
             const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
             const float rlo[3] = {q1.z, q1.w, q2.x}, rhi[3] = {q2.y, q2.z, q2.w};
             float la = tn, lb = tf, ra = tn, rb = tf;
-            slab(r, llo, lhi, la, lb);
-            slab(r, rlo, rhi, ra, rb);
+            slab_tree(r, llo, lhi, la, lb);
+            slab_tree(r, rlo, rhi, ra, rb);
             bool hl = la <= lb, hr = ra <= rb;
             if (hl && hr) {
                 bool left_first = la <= ra;
                 if (sp < STACK) {
-                    sref[sp] = left_first ? q3.y : q3.x;
-                    sta[sp] = left_first ? ra : la;
-                    stb[sp] = left_first ? rb : lb;
+                    stk[sp] = left_first ? make_float4(__int_as_float(q3.y), ra, rb, 0.0f)
+                                         : make_float4(__int_as_float(q3.x), la, lb, 0.0f);
                     ++sp;
                 }
                 ref = left_first ? q3.x : q3.y;
@@ -472,7 +488,7 @@ __device__ __forceinline__ int2 range_get(const int2 (&rg)[RANGES], int i)
 // boundary.
 template <typename T, int SAMPLER, typename Walk>
 __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float tn, float tf,
-                                           Walk &w, Acc &acc, long long &ns)
+                                           Walk &w, Acc &acc, int &ns)
 {
     const unsigned lanes = __activemask();
     int k_next = 0;
@@ -539,8 +555,9 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
 // One pixel: ray, volume interval, traversal of the structure, background.
 // Shared by the plain and the batched kernels, so both give the same bits.
 template <typename T, int SAMPLER, int KIND>
-__device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long long &ns)
+__device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long long &ns_total)
 {
+    int ns = 0;  // samples of this ray (at most 2^24)
     Ray r;
     gen_ray(a, x, y, r);
     float lo[3] = {0.0f, 0.0f, 0.0f};
@@ -565,6 +582,7 @@ __device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long 
             trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
         }
     }
+    ns_total += ns;
     float one_m = 1.0f - acc.a;
     a.out[(size_t)y * a.W + x] =
         make_float4(fmaf(one_m, a.bg[0], acc.r), fmaf(one_m, a.bg[1], acc.g),

@@ -68,6 +68,10 @@ struct ess_server {
     std::deque<Inflight> inflight;
     std::vector<cudaEvent_t> free_events;
     cudaStream_t copy_stream = nullptr;  // image copies overlap the next batch
+    // stream-ordered pool for the per-request output buffers; it keeps up to
+    // the memory budget mapped, so allocations after a synchronisation do not
+    // go back to the driver
+    cudaMemPool_t pool = nullptr;
     std::string error;
 };
 
@@ -161,7 +165,8 @@ void issue(ess_server *s, std::vector<Req *> &batch)
             if (st == ESS_OK) st = ess_rebuild(ctx, q->r.structure);
         }
         if (st == ESS_OK) {
-            if (cudaMallocAsync((void **)&q->dev_out, q->out_bytes, c.stream) != cudaSuccess) {
+            if (cudaMallocFromPoolAsync((void **)&q->dev_out, q->out_bytes, s->pool, c.stream) !=
+                cudaSuccess) {
                 cudaGetLastError();
                 q->dev_out = nullptr;
                 st = ESS_ERR_OOM;
@@ -274,6 +279,18 @@ ess_status ess_server_create(ess_ctx *ctx, const ess_server_config *cfg, ess_ser
         delete s;
         return ESS_ERR_CUDA;
     }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->c.device;
+    uint64_t keep = c.memory_budget;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        cudaStreamDestroy(s->copy_stream);
+        delete s;
+        return ESS_ERR_CUDA;
+    }
     s->worker = std::thread(worker_loop, s);
     *out = s;
     return ESS_OK;
@@ -355,8 +372,10 @@ ess_status ess_server_destroy(ess_server *s)
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->copy_stream);
+    cudaStreamSynchronize(s->ctx->c.stream);
     for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
     cudaStreamDestroy(s->copy_stream);
+    cudaMemPoolDestroy(s->pool);
     delete s;
     return ESS_OK;
 }

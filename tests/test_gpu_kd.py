@@ -55,6 +55,19 @@ def test_kd_nodes_bit_exact(gpu, ctx, ora, case, nbins, halting, mls, B):
     check_kd(gpu, ctx, ora, vf(), lo, hi, tff(), B, nbins, halting, mls)
 
 
+@pytest.mark.parametrize("case", CASES[:2], ids=lambda c: c[0])
+def test_kd_host_loop_equals_graph(gpu, ctx, ora, case, monkeypatch):
+    """ESS_KD_GRAPH=0 (the host-driven level loop that per-kernel profilers
+    need) builds the same tree as the device-driven graph, which itself
+    equals the oracle."""
+    name, vf, (lo, hi), tff = case
+    v, tf = vf(), tff()
+    monkeypatch.setenv("ESS_KD_GRAPH", "0")
+    check_kd(gpu, ctx, ora, v, lo, hi, tf, 8, 4, 1, 32)
+    monkeypatch.setenv("ESS_KD_GRAPH", "1")
+    check_kd(gpu, ctx, ora, v, lo, hi, tf, 8, 4, 1, 32)
+
+
 def test_kd_menger_shallow_single_node(gpu, ctx, ora):
     """Table 1: the Menger sponge's shallow tree is one node (GPU builder)."""
     st, ov, ot = check_kd(gpu, ctx, ora, synth.menger_u8(81), 0, 255, synth.tf_ramp(256, 100),
