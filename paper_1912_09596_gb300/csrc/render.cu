@@ -176,10 +176,30 @@ __device__ __forceinline__ size_t cell_index(const RArgs &a, int ix, int iy, int
     return (size_t)(cz * (a.ny + 1) + cy) * (size_t)(a.nx + 1) + cx;
 }
 
-template <> struct Corners<uint8_t, 1> {
-    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+// One trilinear sample (R2) in two steps: fetch() computes the position, the
+// cell and the weights and loads the cell; value() unpacks the corners and
+// interpolates.
+template <typename T, int SAMPLER> struct CellRaw;
+template <typename T> struct CellRaw<T, 0> {
+    float v[8];
+    __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
-        uint2 c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_index(a, ix, iy, iz));
+        Corners<T, 0>::get(a, ix, iy, iz, v);
+    }
+    __device__ __forceinline__ void corners(const RArgs &, float out[8]) const
+    {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = v[k];
+    }
+};
+template <> struct CellRaw<uint8_t, 1> {
+    uint2 c;
+    __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
+    {
+        c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_index(a, ix, iy, iz));
+    }
+    __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
+    {
         // byte b under the exponent of 2^23 is the float 2^23 + b: exact
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -188,12 +208,15 @@ template <> struct Corners<uint8_t, 1> {
         }
     }
 };
-
-template <> struct Corners<uint16_t, 1> {
-    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+template <> struct CellRaw<uint16_t, 1> {
+    uint4 c;
+    __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
-        uint4 c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_index(a, ix, iy, iz));
-        uint32_t w[4] = {c.x, c.y, c.z, c.w};
+        c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_index(a, ix, iy, iz));
+    }
+    __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
+    {
+        const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             v[2 * k] = __int_as_float(__byte_perm(w[k], 0x4b000000u, 0x7610)) - 8388608.0f;
@@ -201,30 +224,45 @@ template <> struct Corners<uint16_t, 1> {
         }
     }
 };
-
-template <> struct Corners<float, 1> {
-    static __device__ __forceinline__ void get(const RArgs &a, int ix, int iy, int iz, float v[8])
+template <> struct CellRaw<float, 1> {
+    float4 c0, c1;
+    __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
         const float4 *p = reinterpret_cast<const float4 *>(a.cells) + 2 * cell_index(a, ix, iy, iz);
-        float4 c0 = __ldg(p), c1 = __ldg(p + 1);
+        c0 = __ldg(p);
+        c1 = __ldg(p + 1);
+    }
+    __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
+    {
         v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w;
         v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
     }
 };
 
-template <typename T, int SAMPLER>
-__device__ __forceinline__ float sample_value(const RArgs &a, float px, float py, float pz)
-{
-    float qx = px - 0.5f, qy = py - 0.5f, qz = pz - 0.5f;
-    float gxf = floorf(qx), gyf = floorf(qy), gzf = floorf(qz);
-    float fx = qx - gxf, fy = qy - gyf, fz = qz - gzf;
-    float v[8];
-    Corners<T, SAMPLER>::get(a, (int)gxf, (int)gyf, (int)gzf, v);
-    float c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
-    float c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
-    float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
-    return lerpf(c0, c1, fz);
-}
+template <typename T, int SAMPLER> struct SampleFetch {
+    CellRaw<T, SAMPLER> raw;
+    float fx, fy, fz;
+    __device__ __forceinline__ void fetch(const RArgs &a, const Ray &r, float t)
+    {
+        const float px = fmaf(t, r.d[0], r.o[0]), py = fmaf(t, r.d[1], r.o[1]),
+                    pz = fmaf(t, r.d[2], r.o[2]);
+        const float qx = px - 0.5f, qy = py - 0.5f, qz = pz - 0.5f;
+        const float gxf = floorf(qx), gyf = floorf(qy), gzf = floorf(qz);
+        fx = qx - gxf;
+        fy = qy - gyf;
+        fz = qz - gzf;
+        raw.load(a, (int)gxf, (int)gyf, (int)gzf);
+    }
+    __device__ __forceinline__ float value(const RArgs &a) const
+    {
+        float v[8];
+        raw.corners(a, v);
+        const float c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+        const float c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+        const float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
+        return lerpf(c0, c1, fz);
+    }
+};
 
 // The table holds nt + 1 entries, the last a copy of entry nt - 1, so that
 // entry i0 + 1 needs no clamp (with x = nt - 1 the weight w is 0 anyway).
@@ -240,12 +278,11 @@ __device__ __forceinline__ float4 classify(const RArgs &a, float v)
                        fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
 }
 
-// One sample (R6 compositing, R7 early termination); true when A >= ert.
-template <typename T, int SAMPLER>
-__device__ __forceinline__ bool sample_step(const RArgs &a, const Ray &r, float t, Acc &acc)
+// Classification and compositing of one sample value (R5, R6) and early
+// termination (R7); true when A >= ert.
+__device__ __forceinline__ bool composite(const RArgs &a, float value, Acc &acc)
 {
-    float px = fmaf(t, r.d[0], r.o[0]), py = fmaf(t, r.d[1], r.o[1]), pz = fmaf(t, r.d[2], r.o[2]);
-    float4 c = classify(a, sample_value<T, SAMPLER>(a, px, py, pz));
+    float4 c = classify(a, value);
     float tr = (1.0f - acc.a) * c.w;
     acc.r = fmaf(tr, c.x, acc.r);
     acc.g = fmaf(tr, c.y, acc.g);
@@ -261,10 +298,12 @@ __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float 
 {
     float kf = 0.0f;
     for (int k = 0; k < 16777216; ++k, kf += 1.0f) {
-        float t = fmaf(kf, a.dt, tn);
+        const float t = fmaf(kf, a.dt, tn);
         if (!(t < tf)) break;
         ++ns;
-        if (sample_step<T, SAMPLER>(a, r, t, acc)) break;
+        SampleFetch<T, SAMPLER> f;
+        f.fetch(a, r, t);
+        if (composite(a, f.value(a), acc)) break;
     }
 }
 
@@ -467,20 +506,45 @@ template <int KIND, int STACK> struct TreeWalk {
     }
 };
 
-// Collected sample ranges (at most RANGES), kept in registers.  A phase also
-// stops once it holds LOOKAHEAD samples, so that early ray termination wastes
-// little traversal.
+// Collected sample ranges (at most RANGES = 4), kept in four named registers
+// as a queue: appended at the back in collection order, consumed from the
+// front (r0) by shifting.  A phase also stops once it holds LOOKAHEAD
+// samples, so that early ray termination wastes little traversal.
 constexpr int RANGES = 4;
 constexpr int LOOKAHEAD = 48;
 
-__device__ __forceinline__ int2 range_get(const int2 (&rg)[RANGES], int i)
-{
-    int2 v = rg[0];
-#pragma unroll
-    for (int j = 1; j < RANGES; ++j)
-        if (i == j) v = rg[j];
-    return v;
-}
+struct Ranges {
+    int2 r0, r1, r2, r3;
+    int n;
+    __device__ __forceinline__ void clear()
+    {
+        r0 = r1 = r2 = r3 = make_int2(0, -1);
+        n = 0;
+    }
+    __device__ __forceinline__ void append(int k0, int k1)
+    {
+        const int2 v = make_int2(k0, k1);
+        if (n == 0) r0 = v;
+        else if (n == 1) r1 = v;
+        else if (n == 2) r2 = v;
+        else r3 = v;
+        ++n;
+    }
+    __device__ __forceinline__ void extend_last(int k1)
+    {
+        if (n == 1) r0.y = k1;
+        else if (n == 2) r1.y = k1;
+        else if (n == 3) r2.y = k1;
+        else r3.y = k1;
+    }
+    __device__ __forceinline__ void pop_front()
+    {
+        r0 = r1;
+        r1 = r2;
+        r2 = r3;
+        --n;
+    }
+};
 
 // Interval-by-interval skipping with phases: collect, then march.  The outer
 // loop is uniform over the lanes that entered together (__any_sync), and the
@@ -494,12 +558,12 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
     int k_next = 0;
     bool alive = true;
     while (__any_sync(lanes, alive)) {
-        int2 rg[RANGES];
-        int nr = 0;
+        Ranges rg;
+        rg.clear();
         if (alive) {
             int held = 0;
             float ta, tb;
-            while (nr < RANGES && held < LOOKAHEAD) {
+            while (rg.n < RANGES && held < LOOKAHEAD) {
                 if (!w.next(a, r, tn, tf, ta, tb)) break;
                 float ka = ceilf((ta - tn) / a.dt) - 1.0f;
                 float kb = floorf((tb - tn) / a.dt) + 1.0f;
@@ -507,40 +571,35 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
                 int k0 = ka > (float)k_next ? (int)ka : k_next;
                 int k1 = (int)kb;
                 if (k1 >= k0) {
-                    bool merge = nr > 0 && k0 == k_next;  // touches the previous range
-#pragma unroll
-                    for (int j = 0; j < RANGES; ++j) {
-                        if (merge && j == nr - 1) rg[j].y = k1;
-                        if (!merge && j == nr) rg[j] = make_int2(k0, k1);
-                    }
-                    if (!merge) ++nr;
+                    if (rg.n > 0 && k0 == k_next) rg.extend_last(k1);  // touches the previous range
+                    else rg.append(k0, k1);
                     held += k1 - k0 + 1;
                     k_next = k1 + 1;
                 }
             }
-            if (nr == 0) alive = false;
+            if (rg.n == 0) alive = false;
         }
         if (alive) {
             // march the collected ranges in increasing k
-            int i = 0;
-            int2 cur = rg[0];
-            int k = cur.x;
+            int k = rg.r0.x;
             float kf = (float)k;
             while (true) {
-                float t = fmaf(kf, a.dt, tn);
+                const float t = fmaf(kf, a.dt, tn);
                 if (!(t < tf)) {
                     alive = false;
                     break;
                 }
                 ++ns;
-                if (sample_step<T, SAMPLER>(a, r, t, acc)) {
+                SampleFetch<T, SAMPLER> f;
+                f.fetch(a, r, t);
+                if (composite(a, f.value(a), acc)) {
                     alive = false;
                     break;
                 }
-                if (k == cur.y) {
-                    if (++i >= nr) break;
-                    cur = range_get(rg, i);
-                    k = cur.x;
+                if (k == rg.r0.y) {
+                    rg.pop_front();
+                    if (rg.n == 0) break;
+                    k = rg.r0.x;
                     kf = (float)k;
                 } else {
                     ++k;
