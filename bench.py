@@ -514,6 +514,62 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
     }
 
 
+def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
+    """The per-brick min/max pass (rebuild with rescan) over larger volumes and
+    every dtype: device time per launch with L2 flushed before each, against
+    the measured HBM peak on the algorithmic bytes (the volume once plus the
+    min/max pairs)."""
+    from paper_1912_09596_gb300 import synth
+    peak, src = measured_peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    rows = []
+    for name, dims in (("u8", (512, 512, 512)), ("u16", (512, 512, 512)), ("f32", (512, 512, 512)),
+                       ("f32", (1024, 1024, 1024))):
+        if name == "u8":
+            x = torch.randint(0, 256, dims, device=dev, dtype=torch.uint8, generator=g)
+            lo, hi = 0, 255
+        elif name == "u16":
+            x = torch.randint(0, 256, dims[:2] + (2 * dims[2],), device=dev, dtype=torch.uint8,
+                              generator=g).view(torch.uint16)
+            lo, hi = 0, 65535
+        else:
+            x = torch.rand(dims, device=dev, dtype=torch.float32, generator=g)
+            lo, hi = 0.0, 1.0
+        vol = ess.ess_volume_upload(ctx, x, lo, hi)
+        ess.ess_volume_set_sampler(ctx, vol, 0)
+        tf = ess.ess_tf_set(ctx, synth.tf_ramp(256, 40))
+        for B in (8, 16, 32):
+            st = ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, rescan=1))
+            for _ in range(2):
+                ess.ess_rebuild(ctx, st)
+            ess.ess_sync(ctx)
+            ess.ess_profile_reset(ctx)
+            ess.ess_profile_enable(ctx, True)
+            for _ in range(reps):
+                flush.zero_()
+                ess.ess_rebuild(ctx, st)
+            ess.ess_sync(ctx)
+            ess.ess_profile_enable(ctx, False)
+            n, ms = ess.ess_profile_read(ctx)["brick_minmax"]
+            nb = 1
+            for d in dims:
+                nb *= (d + B - 1) // B
+            byts = x.numel() * x.element_size() + 8 * nb
+            gbs = byts / (ms / n / 1000.0) / 1e9
+            rows.append({"dtype": name, "dims": "%dx%dx%d" % dims[::-1], "brick": B,
+                         "us": round(1000.0 * ms / n, 2), "achieved_gbs": round(gbs, 1),
+                         "frac": round(gbs / peak, 3)})
+            ess.ess_release(ctx, st)
+        ess.ess_release(ctx, tf)
+        ess.ess_release(ctx, vol)
+        del x
+        torch.cuda.empty_cache()
+    return {"kernel": "brick_minmax", "peak_gbs": peak, "peak_source": src,
+            "l2": "flushed before each launch", "rows": rows}
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args, rank, local, ws, dist):
     import torch
@@ -724,6 +780,9 @@ def run_ours(args, rank, local, ws, dist):
     if not args.no_serve:
         with torch.cuda.stream(stream):
             result["served"] = run_served(ess, torch, dev, ctx, vol_np)
+    if not args.no_minmax:
+        with torch.cuda.stream(stream):
+            result["minmax_sweep"] = run_minmax_sweep(ess, torch, dev, ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
         rate, desc = oracle_rate(vol_np, vlo, vhi, tfs_np[0], cams[0], w, args.ref_budget, cores)
@@ -749,6 +808,8 @@ def main():
                     help="skip the batched-render comparison (64 TFs x 4 views)")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving comparison (Poisson request stream)")
+    ap.add_argument("--no-minmax", action="store_true",
+                    help="skip the brick min/max sweep over dtypes and sizes")
     args = ap.parse_args()
     rank, local, ws, dist = dist_setup()
     if args.impl == "reference":

@@ -302,17 +302,32 @@ template <> struct ColMinMax<float> {
     }
 };
 
-constexpr int MM_WARPS = 2;  // warps per unit
 constexpr int MM_SLOT = 34;  // 16-byte vectors per row slot: 32 lanes + 2 edge vectors
 
 // Pipeline shape for brick size B: a step moves a block of R consecutive
 // rows of one z plane, NB blocks cover the plane's B + 2 apron rows, and a
-// warp keeps DEPTH steps (about 20 rows) in flight.  Interior units have an
-// even number B + 2 of planes, so the two warps get equal shares.
+// warp keeps DEPTH steps (about 20 rows) in flight.  Larger bricks mean
+// fewer units with more rows each, so a unit gets more warps: 2 up to 8^3,
+// 4 at 16^3, 8 beyond.  The (B + 2) * NB steps of an interior unit divide
+// evenly among them for B <= 32.
 template <int B> struct MmShape {
     static constexpr int NB = (B + 2 + 9) / 10;
     static constexpr int R = (B + 2 + NB - 1) / NB;
     static constexpr int DEPTH = 20 / R > 2 ? 20 / R : 2;
+    static constexpr int WARPS = B <= 8 ? 2 : (B <= 16 ? 4 : 8);
+};
+
+// Shared memory of one unit (dynamic: above 48 KiB for the 8-warp units).
+// Per warp: the ring of DEPTH steps, later reused for the merge of its
+// columns (2 VPL + 2 floats per lane).
+template <typename T, int B> struct MmSmem {
+    static constexpr int VPL = 16 / (int)sizeof(T);
+    static constexpr int ROW_BYTES = MM_SLOT * 16;
+    static constexpr int STEP_BYTES = MmShape<B>::R * ROW_BYTES;
+    static constexpr int RING_BYTES = MmShape<B>::DEPTH * STEP_BYTES;
+    static constexpr int MERGE_BYTES = (2 * VPL + 2) * 32 * 4;
+    static constexpr int WARP_BYTES = RING_BYTES > MERGE_BYTES ? RING_BYTES : MERGE_BYTES;
+    static constexpr int BYTES = MmShape<B>::WARPS * WARP_BYTES;
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t smem, const void *gmem)
@@ -334,20 +349,19 @@ __device__ __forceinline__ uint4 lds16(uint32_t smem)
     return v;
 }
 template <typename T, int B>
-__global__ void __launch_bounds__(MM_WARPS * 32) k_brick_minmax_vec(const T *__restrict__ vol, int nx,
+__global__ void __launch_bounds__(MmShape<B>::WARPS * 32) k_brick_minmax_vec(const T *__restrict__ vol, int nx,
                                                                     int ny, int nz, int gx, int gy,
                                                                     int gz, float2 *__restrict__ out)
 {
     constexpr int VPL = 16 / (int)sizeof(T);
     constexpr int R = MmShape<B>::R, NB = MmShape<B>::NB, DEPTH = MmShape<B>::DEPTH;
-    constexpr int NCOL = 2 * VPL + 2;  // merged floats per lane: columns min/max, edge min/max
-    constexpr int ROW_BYTES = MM_SLOT * 16;
-    constexpr int STEP_BYTES = R * ROW_BYTES;
-    constexpr int RING_BYTES = DEPTH * STEP_BYTES;
-    constexpr int MERGE_BYTES = NCOL * 32 * 4;
-    constexpr int WARP_BYTES = RING_BYTES > MERGE_BYTES ? RING_BYTES : MERGE_BYTES;
+    constexpr int MM_WARPS = MmShape<B>::WARPS;
+    constexpr int ROW_BYTES = MmSmem<T, B>::ROW_BYTES;
+    constexpr int STEP_BYTES = MmSmem<T, B>::STEP_BYTES;
+    constexpr int RING_BYTES = MmSmem<T, B>::RING_BYTES;
+    constexpr int WARP_BYTES = MmSmem<T, B>::WARP_BYTES;
     static_assert(NB * R >= B + 2, "blocks must cover the apron rows");
-    __shared__ __align__(16) unsigned char smem[MM_WARPS * WARP_BYTES];
+    extern __shared__ __align__(16) unsigned char smem[];  // MmSmem<T, B>::BYTES
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int row_vecs = nx / VPL;
     const int nchunk = (row_vecs + 31) >> 5;
@@ -521,8 +535,12 @@ bool launch_minmax_vec(Ctx &c, const T *data, int nx, int ny, int nz, int B, int
     Launch L(c, "brick_minmax");
 #define ESS_MMV(BB)                                                                           \
     case BB:                                                                                  \
-        k_brick_minmax_vec<T, BB>                                                             \
-            <<<blocks, MM_WARPS * 32, 0, c.stream>>>(data, nx, ny, nz, gx, gy, gz, out);      \
+        if (MmSmem<T, BB>::BYTES > 48 * 1024)                                                 \
+            ESS_CUDA(cudaFuncSetAttribute(k_brick_minmax_vec<T, BB>,                          \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                          MmSmem<T, BB>::BYTES));                             \
+        k_brick_minmax_vec<T, BB><<<blocks, MmShape<BB>::WARPS * 32, MmSmem<T, BB>::BYTES,      \
+                                    c.stream>>>(data, nx, ny, nz, gx, gy, gz, out);           \
         return true;
     switch (B) {
         ESS_MMV(2)
