@@ -113,6 +113,7 @@ struct Structure {
     uint32_t *sort_scratch = nullptr;
     int32_t *left = nullptr, *right = nullptr, *parent = nullptr, *leaf_parent = nullptr;
     int32_t *inner_box = nullptr;  // (n-1) x 6
+    int32_t *inner_cnt = nullptr;  // (n-1): leaves under each inner node
     int *arrive = nullptr;
     BoxNode *nodes = nullptr;      // traversal nodes (LBVH: n-1; k-d: inner nodes)
     int32_t *root = nullptr;       // device root record: ref, then the box as 6 floats (voxels)

@@ -272,6 +272,13 @@ __global__ void k_karras(const uint32_t *__restrict__ k, const int *__restrict__
 // unions the two child boxes, writes the node's box and its traversal node,
 // and climbs on.  Writers fence before the arrival counter; readers load with
 // .cg so that they see boxes written on other SMs.
+//
+// Solid subtrees: an inner node whose leaf count equals the number of bricks
+// in its box covers that box with non-empty bricks and nothing else, so the
+// ray's interval through the box is exactly the union of the leaves'
+// intervals.  Its parent's traversal node refers to it as a leaf (a negative
+// reference), and the traversal yields the box's interval without
+// descending.  The topology arrays (left, right, boxes) are unchanged.
 __device__ __forceinline__ void brick_box(uint32_t b, int gx, int gy, int32_t box[6])
 {
     int x = (int)(b % (uint32_t)gx), y = (int)((b / (uint32_t)gx) % (uint32_t)gy);
@@ -281,6 +288,18 @@ __device__ __forceinline__ void brick_box(uint32_t b, int gx, int gy, int32_t bo
 }
 
 // root record: ref, then the box in voxel units as float bits
+// Leaf reference standing for a solid subtree: the brick at its low corner
+// (any brick id marks a leaf for the traversal, which uses the box alone).
+__device__ __forceinline__ int32_t solid_ref(const int32_t box[6], int gx, int gy)
+{
+    return -1 - (int32_t)(((int64_t)box[2] * gy + box[1]) * gx + box[0]);
+}
+
+__device__ __forceinline__ bool solid(int32_t cnt, const int32_t box[6])
+{
+    return (int64_t)cnt == (int64_t)(box[3] - box[0]) * (box[4] - box[1]) * (box[5] - box[2]);
+}
+
 __device__ __forceinline__ void write_root(int32_t *root, int32_t ref, const int32_t box[6], int B)
 {
     root[0] = ref;
@@ -292,8 +311,8 @@ __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int
                               const int32_t *__restrict__ left, const int32_t *__restrict__ right,
                               const int32_t *__restrict__ parent,
                               const int32_t *__restrict__ leaf_parent, int *arrive,
-                              int32_t *inner_box, BoxNode *nodes, int32_t *root, int gx, int gy,
-                              int B)
+                              int32_t *inner_box, int32_t *inner_cnt, BoxNode *nodes,
+                              int32_t *root, int gx, int gy, int B)
 {
     int n = *count;
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -313,18 +332,22 @@ __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int
         __threadfence();
         int32_t lb[6], rb[6];
         int lc = __ldcg(left + p), rc = __ldcg(right + p);
+        int32_t lcnt = 1, rcnt = 1;
         if (lc < 0) {
             brick_box(__ldg(sorted_ids + (-1 - lc)), gx, gy, lb);
         } else {
 #pragma unroll
             for (int a = 0; a < 6; ++a) lb[a] = __ldcg(inner_box + 6 * lc + a);
+            lcnt = __ldcg(inner_cnt + lc);
         }
         if (rc < 0) {
             brick_box(__ldg(sorted_ids + (-1 - rc)), gx, gy, rb);
         } else {
 #pragma unroll
             for (int a = 0; a < 6; ++a) rb[a] = __ldcg(inner_box + 6 * rc + a);
+            rcnt = __ldcg(inner_cnt + rc);
         }
+        inner_cnt[p] = lcnt + rcnt;
         BoxNode nd;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -337,11 +360,13 @@ __global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int
             nd.lbox[a] = (float)(lb[a] * B);
             nd.rbox[a] = (float)(rb[a] * B);
         }
-        nd.left = lc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - lc)) : lc;
-        nd.right = rc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - rc)) : rc;
+        nd.left = lc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - lc))
+                         : (solid(lcnt, lb) ? solid_ref(lb, gx, gy) : lc);
+        nd.right = rc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - rc))
+                          : (solid(rcnt, rb) ? solid_ref(rb, gx, gy) : rc);
         nd.pad0 = nd.pad1 = 0;
         nodes[p] = nd;
-        if (p == 0) write_root(root, 0, box, B);
+        if (p == 0) write_root(root, solid(lcnt + rcnt, box) ? solid_ref(box, gx, gy) : 0, box, B);
         p = __ldcg(parent + p);
     }
 }
@@ -392,8 +417,8 @@ void launch_lbvh(Ctx &c, Structure &s)
         Launch L(c, "lbvh_bounds");
         k_lbvh_bounds<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
                                                     s.parent, s.leaf_parent, s.arrive,
-                                                    s.inner_box, s.nodes, s.root, s.gx, s.gy,
-                                                    s.p.brick);
+                                                    s.inner_box, s.inner_cnt, s.nodes, s.root,
+                                                    s.gx, s.gy, s.p.brick);
     }
 }
 
