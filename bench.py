@@ -514,6 +514,43 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
     }
 
 
+def run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, steps=3):
+    """The hybrid grid (Sec. 3.3: a shallow k-d tree whose leaves are crossed
+    with the macrocell grid) on the main workload's TF edits: rebuild and one
+    frame per edit, CUDA-event time per kernel, for 16^3 and 8^3 bricks."""
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    res = {}
+    for B in (16, 8):
+        st = ess.ess_build(ctx, vol, tf, ess.HYBRID, ess.build_params(brick=B, nbins=4, halting=0))
+        for i in range(len(tf_dev)):      # warm-up pass
+            ess.ess_tf_update(ctx, tf, tf_dev[i])
+            ess.ess_rebuild(ctx, st)
+            ess.ess_render(ctx, st, ecams[i], rp, W, H, out)
+        ess.ess_sync(ctx)
+        ess.ess_sample_count(ctx, reset=True)
+        ess.ess_profile_reset(ctx)
+        ess.ess_profile_enable(ctx, True)
+        for _ in range(steps):
+            for i in range(len(tf_dev)):
+                ess.ess_tf_update(ctx, tf, tf_dev[i])
+                ess.ess_rebuild(ctx, st)
+                ess.ess_render(ctx, st, ecams[i], rp, W, H, out)
+        ess.ess_sync(ctx)
+        ess.ess_profile_enable(ctx, False)
+        prof = ess.ess_profile_read(ctx)
+        frames = steps * len(tf_dev)
+        n, ms = prof["render_hybrid"]
+        build = sum(v[1] for k, v in prof.items() if not k.startswith("render")) / frames
+        info = ess.ess_structure_info_get(ctx, st)
+        res["brick%d" % B] = {"ms_per_frame": round(ms / n, 4), "build_ms_per_edit": round(build, 4),
+                              "kd_nodes_last_edit": info["n_nodes"],
+                              "samples_per_frame": ess.ess_sample_count(ctx, reset=True) / frames}
+        ess.ess_release(ctx, st)
+    return {"structure": "hybrid grid: shallow k-d tree (halting 0, 3 binned planes per axis) "
+                         "whose leaves are crossed with the macrocell grid of the same brick size",
+            "workload": "the main workload's 8 TF edits, one rebuild and one frame each", **res}
+
+
 def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
     """The per-brick min/max pass (rebuild with rescan) over larger volumes and
     every dtype: device time per launch with L2 flushed before each, against
@@ -774,6 +811,8 @@ def run_ours(args, rank, local, ws, dist):
                 "ms_per_step": e2e_ms / args.steps},
         "clocks": clk,
     }
+    with torch.cuda.stream(stream):
+        result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
     if not args.no_batched:
         with torch.cuda.stream(stream):
             result["batched"] = run_batched(ess, torch, dev, stream, ctx)

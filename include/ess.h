@@ -59,7 +59,10 @@ typedef enum {
     ESS_GRID = 0,  /* uniform macrocell grid = the brick mask (Sec. 1, 2) */
     ESS_LBVH = 1,  /* LBVH over non-empty bricks (Sec. 3.1) */
     ESS_KD = 2,    /* k-d tree with tight boxes (Sec. 3.2) */
-    ESS_NONE = 3   /* no skipping: naive ray marching (Table 2, "Naive") */
+    ESS_NONE = 3,  /* no skipping: naive ray marching (Table 2, "Naive") */
+    ESS_HYBRID = 4 /* hybrid grid (Sec. 3.3): a k-d tree (the paper's is shallow,
+                      halting 0) whose leaves are crossed with the macrocell grid
+                      of the same brick size */
 } ess_kind;
 
 /* ---------------------------------------------------------------- context */
@@ -146,7 +149,8 @@ typedef struct {
 
 /* Builds a skipping structure of `kind` for volume `vol` under TF `tf`
  * (Sec. 3).  For ESS_NONE no index is built; the handle just binds the
- * volume and the TF for naive rendering.  The structure keeps references to
+ * volume and the TF for naive rendering.  ESS_HYBRID runs the k-d build with
+ * `params` and keeps the brick mask as its global grid.  The structure keeps references to
  * `vol` and `tf`.  Asynchronous except for the k-d build, which reads back
  * one node count per tree level.  Errors: ESS_ERR_ARG for bad parameters,
  * ESS_ERR_HANDLE for bad handles, ESS_ERR_OOM. */
@@ -247,7 +251,7 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
 /* ------------------------------------------------------------------ tuning */
 
 typedef struct {
-    int kind;      /* ESS_GRID, ESS_LBVH or ESS_KD */
+    int kind;      /* ESS_GRID, ESS_LBVH, ESS_KD or ESS_HYBRID */
     int brick;     /* brick edge */
     int tile_w;    /* warp tile width for ess_render_params.tile_w */
     float build_ms, render_ms;  /* measured: one rebuild, mean of one frame per camera */

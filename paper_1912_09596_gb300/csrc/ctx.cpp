@@ -293,7 +293,7 @@ void run_build(Ctx &c, Structure &s)
     s.n_host = -1;
     s.height = -1;
     if (s.kind == ESS_LBVH) launch_lbvh(c, s);
-    if (s.kind == ESS_KD) {
+    if (s.kind == ESS_KD || s.kind == ESS_HYBRID) {
         s.volume = &v;
         launch_kd(c, s);
     }
@@ -556,7 +556,8 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         ESS_REQUIRE(structure, "null pointer");
         Volume &v = get_vol(c, vol);
         TF &t = get_tf(c, tf);
-        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_KD || kind == ESS_NONE,
+        ESS_REQUIRE(kind == ESS_GRID || kind == ESS_LBVH || kind == ESS_KD || kind == ESS_NONE ||
+                        kind == ESS_HYBRID,
                     "unknown structure kind");
         ess_build_params p = params ? *params : ess_build_params{8, 4, 1, 0, 0, 0};
         auto s = std::make_unique<Structure>();
@@ -591,7 +592,7 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
             }
             try {
                 if (kind == ESS_LBVH) alloc_lbvh(c, *s);
-                if (kind == ESS_KD) alloc_kd(c, *s);
+                if (kind == ESS_KD || kind == ESS_HYBRID) alloc_kd(c, *s);
             } catch (...) {
                 free_structure(c, *s);
                 throw;
@@ -646,7 +647,7 @@ ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_struct
             if (s.height < 0) s.height = n > 0 ? lbvh_height(c, s) : 0;
             info->height = s.height;
         }
-        if (s.kind == ESS_KD) {
+        if (s.kind == ESS_KD || s.kind == ESS_HYBRID) {
             kd_stats(c, s);
             info->n_nodes = s.kd_count;
             info->height = s.height;
@@ -693,7 +694,7 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
             break;
         }
         case ESS_ARR_KD_NODES:
-            ESS_REQUIRE(s.kind == ESS_KD, "array only exists for a k-d tree");
+            ESS_REQUIRE(s.kind == ESS_KD || s.kind == ESS_HYBRID, "array only exists for a k-d tree");
             kd_stats(c, s);
             copy_out(c, dst, s.kd_nodes, sizeof(int32_t) * 9 * (size_t)s.kd_count, capacity, written);
             break;
@@ -849,7 +850,7 @@ ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_c
         cudaEvent_t e0, e1;
         ESS_CUDA(cudaEventCreate(&e0));
         ESS_CUDA(cudaEventCreate(&e1));
-        const int kinds[3] = {ESS_GRID, ESS_LBVH, ESS_KD};
+        const int kinds[4] = {ESS_GRID, ESS_LBVH, ESS_KD, ESS_HYBRID};
         const int bricks[4] = {4, 8, 16, 32};
         const int tiles[4] = {4, 8, 16, 32};
         double best_cost = 1e300;
@@ -857,7 +858,8 @@ ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_c
         std::string err;
         for (int kind : kinds) {
             for (int B : bricks) {
-                ess_build_params bp{B, 4, 1, 32, 0, 0};
+                // the hybrid's tree is the paper's shallow one
+                ess_build_params bp{B, 4, kind == ESS_HYBRID ? 0 : 1, kind == ESS_HYBRID ? 0 : 32, 0, 0};
                 ess_handle h = 0;
                 if (ess_build(ctx, vol, tf, (ess_kind)kind, &bp, &h) != ESS_OK) {
                     c.last_error.clear();

@@ -506,6 +506,47 @@ template <int KIND, int STACK> struct TreeWalk {
     }
 };
 
+// Hybrid grid (Sec. 3.3): ordered traversal of the k-d tree yields the
+// leaves' intervals; inside each leaf interval the 3-D DDA over the brick
+// raster (the macrocell grid) yields the intervals of the leaf's non-empty
+// bricks.  Leaves are unions of bricks and come front to back, and the DDA
+// runs front to back inside each, so the intervals come in ray order; they
+// cover the same non-empty bricks as the grid's walk.
+struct HybridWalk {
+    TreeWalk<ESS_KD, 128> tree;
+    GridWalk grid;
+    float leaf_tb;
+    bool in_leaf;
+
+    __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn, float tf)
+    {
+        tree.init(a, r, tn, tf);
+        in_leaf = false;
+    }
+
+    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+                                         float &tb)
+    {
+        bool hit = false;
+        bool more = true;
+        while (!hit && more) {
+            if (in_leaf) {
+                hit = grid.next(a, r, tn, leaf_tb, ta, tb);
+                if (!hit) in_leaf = false;
+            } else {
+                float la, lb;
+                more = tree.next(a, r, tn, tf, la, lb);
+                if (more) {
+                    grid.init(a, r, la);
+                    leaf_tb = lb;
+                    in_leaf = true;
+                }
+            }
+        }
+        return hit;
+    }
+};
+
 // Collected sample ranges (at most RANGES = 4), kept in four named registers
 // as a queue: appended at the back in collection order, consumed from the
 // front (r0) by shifting.  A phase also stops once it holds LOOKAHEAD
@@ -630,6 +671,10 @@ __device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long 
         } else if (KIND == ESS_GRID) {
             GridWalk w;
             w.init(a, r, tn);
+            trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
+        } else if (KIND == ESS_HYBRID) {
+            HybridWalk w;
+            w.init(a, r, tn, tf);
             trace_walk<T, SAMPLER>(a, r, tn, tf, w, acc, ns);
         } else if (KIND == ESS_LBVH) {
             TreeWalk<ESS_LBVH, 32> w;
@@ -776,7 +821,7 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.gz = j.st->gz;
     a.nodes = j.st->nodes;
     a.root = j.st->root;
-    a.count = j.st->kind == ESS_KD ? j.st->kd_count_dev : j.st->count;
+    a.count = (j.st->kind == ESS_KD || j.st->kind == ESS_HYBRID) ? j.st->kd_count_dev : j.st->count;
     a.samples = c.samples;
 }
 
@@ -786,6 +831,7 @@ static const char *render_name(int kind)
     case ESS_NONE: return "render_naive";
     case ESS_GRID: return "render_grid";
     case ESS_LBVH: return "render_lbvh";
+    case ESS_HYBRID: return "render_hybrid";
     default: return "render_kd";
     }
 }
@@ -805,6 +851,7 @@ void launch_render(Ctx &c, const RenderJob &j)
     case ESS_NONE: launch_kind<ESS_NONE>(c, a, j.vol->dtype, tw); break;
     case ESS_GRID: launch_kind<ESS_GRID>(c, a, j.vol->dtype, tw); break;
     case ESS_LBVH: launch_kind<ESS_LBVH>(c, a, j.vol->dtype, tw); break;
+    case ESS_HYBRID: launch_kind<ESS_HYBRID>(c, a, j.vol->dtype, tw); break;
     default: launch_kind<ESS_KD>(c, a, j.vol->dtype, tw); break;
     }
 }
@@ -878,6 +925,7 @@ void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, void *dev)
     case ESS_NONE: ESS_BATCH_T(ESS_NONE); break;
     case ESS_GRID: ESS_BATCH_T(ESS_GRID); break;
     case ESS_LBVH: ESS_BATCH_T(ESS_LBVH); break;
+    case ESS_HYBRID: ESS_BATCH_T(ESS_HYBRID); break;
     default: ESS_BATCH_T(ESS_KD); break;
     }
 #undef ESS_BATCH_T

@@ -22,9 +22,10 @@ LIB_PATH = os.path.join(_HERE, "libess.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_HANDLE, ERR_TIMEOUT, ERR_BUSY, ERR_STALE = 0, -1, -2, -3, -4, -5, -6, -7
 U8, U16, F32 = 0, 1, 2
-GRID, LBVH, KD, NONE = 0, 1, 2, 3
-KIND_NAMES = {GRID: "grid", LBVH: "lbvh", KD: "kd", NONE: "none"}
-KINDS = (NONE, GRID, LBVH, KD)   # structure kinds this library builds
+GRID, LBVH, KD, NONE, HYBRID = 0, 1, 2, 3, 4
+KIND_NAMES = {GRID: "grid", LBVH: "lbvh", KD: "kd", NONE: "none", HYBRID: "hybrid"}
+KINDS = (NONE, GRID, LBVH, KD)   # the paper's three structures and the naive marcher
+ALL_KINDS = KINDS + (HYBRID,)    # with the hybrid grid (Sec. 3.3)
 (ARR_MINMAX, ARR_MASK, ARR_IDS, ARR_KEYS, ARR_SORTED_KEYS, ARR_SORTED_IDS, ARR_LBVH_LEFT,
  ARR_LBVH_RIGHT, ARR_LBVH_BOXES, ARR_KD_NODES) = range(10)
 

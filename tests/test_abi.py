@@ -51,3 +51,18 @@ def test_null_context_is_rejected(libpath):
     assert ess.lib.ess_sync(None) == ess.ERR_ARG
     assert ess.lib.ess_destroy(None) == ess.ERR_ARG
     assert ess.ess_launch_count(None) == 0
+
+
+def test_binding_constants_match_header(libpath):
+    """Every `ESS_NAME = value` enumerator in include/*.h has the same value
+    as the binding's NAME constant (structure kinds, dtypes, arrays, status
+    codes, request kinds)."""
+    from paper_1912_09596_gb300 import ess
+    found = 0
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, value in re.findall(r"\bESS_(\w+)\s*=\s*(-?\d+)", src):
+            assert hasattr(ess, name), "binding lacks %s" % name
+            assert getattr(ess, name) == int(value), name
+            found += 1
+    assert found >= 20

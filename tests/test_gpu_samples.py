@@ -4,8 +4,8 @@ Image parity cannot see a traversal that marches through empty space: the
 extra samples there have zero opacity and leave the image unchanged.  So the
 number of samples each structure's render takes (early termination off) is
 compared with the oracle's brute-force rule-S enumeration over the
-structure's leaf boxes: non-empty bricks for the grid and the LBVH, leaf boxes
-for the k-d tree.  The GPU slab tests and DDA crossings round differently from
+structure's leaf boxes: non-empty bricks for the grid, the LBVH and the
+hybrid grid, leaf boxes for the k-d tree.  The GPU slab tests and DDA crossings round differently from
 the oracle's, which can move the sample taken at either end of an interval,
 hence a small relative tolerance."""
 import numpy as np
@@ -37,11 +37,14 @@ def test_sample_counts_match_oracle_boxes(gpu, ctx, ora, case, B):
     grid = ov.grid(B)
     boxes = {ess.GRID: ora.brick_boxes(np.nonzero(mask)[0], grid, B, ov.dims)}
     boxes[ess.LBVH] = boxes[ess.GRID]
+    boxes[ess.HYBRID] = boxes[ess.GRID]  # the grid inside the tree's leaves
     rng = np.random.default_rng(B)
     W, H = 80, 64
     cams = [synth.orbit_camera(v.shape[::-1], W, H, 0.7), synth.random_camera(v.shape[::-1], rng)]
-    for kind in (ess.GRID, ess.LBVH, ess.KD):
-        st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=B, nbins=4, halting=1, mls=32))
+    for kind in (ess.GRID, ess.LBVH, ess.KD, ess.HYBRID):
+        halting, mls = (0, 0) if kind == ess.HYBRID else (1, 32)
+        st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=B, nbins=4, halting=halting,
+                                                               mls=mls))
         if kind == ess.KD:
             nodes = ess.ess_structure_read(ctx, st, ess.ARR_KD_NODES).reshape(-1, 9)
             boxes[kind] = ora.kd_leaf_boxes(nodes, B, ov.dims)
