@@ -811,8 +811,9 @@ def run_ours(args, rank, local, ws, dist):
                 "ms_per_step": e2e_ms / args.steps},
         "clocks": clk,
     }
-    with torch.cuda.stream(stream):
-        result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
+    if not args.no_hybrid:
+        with torch.cuda.stream(stream):
+            result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
     if not args.no_batched:
         with torch.cuda.stream(stream):
             result["batched"] = run_batched(ess, torch, dev, stream, ctx)
@@ -849,6 +850,8 @@ def main():
                     help="skip the serving comparison (Poisson request stream)")
     ap.add_argument("--no-minmax", action="store_true",
                     help="skip the brick min/max sweep over dtypes and sizes")
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="skip the hybrid-grid leg")
     args = ap.parse_args()
     rank, local, ws, dist = dist_setup()
     if args.impl == "reference":

@@ -552,7 +552,7 @@ struct HybridWalk {
 // front (r0) by shifting.  A phase also stops once it holds LOOKAHEAD
 // samples, so that early ray termination wastes little traversal.
 constexpr int RANGES = 4;
-constexpr int LOOKAHEAD = 48;
+constexpr int LOOKAHEAD = 64;
 
 struct Ranges {
     int2 r0, r1, r2, r3;
