@@ -214,7 +214,8 @@ def render_naive(vol: OVolume, tf: OTF, cam, W, H, dt=0.5, ert=2.0,
 
 def render_pixels(vol: OVolume, tf: OTF, cam, W, H, xy, dt=0.5, ert=2.0,
                   bg=(0.0, 0.0, 0.0, 0.0), threads=1):
-    """Naive marching of the pixels `xy` ((n, 2) int: x, y).  Returns (n, 4)."""
+    """Naive marching of the pixels `xy` ((n, 2) int: x, y).  Returns the
+    (n, 4) pixels and the number of samples taken."""
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
     out = np.zeros((xy.shape[0], 4), dtype=np.float32)
     cs, ps = camera_struct(cam), params_struct(dt, ert, bg)

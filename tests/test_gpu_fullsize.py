@@ -1,0 +1,95 @@
+"""Parity at the benchmark's full sizes, on outputs the oracle can compute
+one by one: the brick masks of the 512^3 CT-like workload (every brick),
+and sampled pixels of full frames rendered in the benchmark's launch
+configuration (512^3 u8 at 1024^2, 1024^3 f32 at 1920x1080), each checked
+against the oracle's naive marching of that pixel."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1912_09596_gb300 import synth
+from gpu_util import TOL, bits
+
+pytestmark = pytest.mark.gpu
+
+
+def _pixels(W, H, n, seed):
+    rng = np.random.default_rng(seed)
+    xy = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], axis=1)
+    fixed = np.array([[0, 0], [W - 1, 0], [0, H - 1], [W - 1, H - 1], [W // 2, H // 2],
+                      [W // 2 - 1, H // 2], [W // 3, 2 * H // 3], [2 * W // 3, H // 3]])
+    return np.concatenate([fixed, xy]).astype(np.int32)
+
+
+def _check_pixels(img, xy, ref, what):
+    got = img[xy[:, 1], xy[:, 0]]
+    if np.array_equal(bits(got), bits(ref)):
+        return
+    diff = float(np.abs(got.astype(np.float64) - ref.astype(np.float64)).max())
+    assert diff <= TOL, "%s: sampled pixels differ by %g" % (what, diff)
+
+
+@pytest.fixture(scope="module")
+def ct512():
+    """The 512^3 CT-like workload of the benchmark: volume, 8 TFs, cameras."""
+    dims = (512, 512, 512)
+    vol = synth.ct_like_u8(dims, seed=1)
+    tfs = synth.tf_set_ct(256)
+    cams = [synth.orbit_camera(dims, 1024, 1024, theta=2 * math.pi * i / len(tfs), phi=0.35,
+                               dist=1.6) for i in range(len(tfs))]
+    return vol, tfs, cams
+
+
+def test_ct512_masks_and_sampled_pixels(gpu, ctx, ora, ct512):
+    ess, torch = gpu
+    vol_np, tfs, cams = ct512
+    W = H = 1024
+    ov = ora.OVolume(vol_np, 0, 255)
+    mm = {B: ora.brick_minmax(ov, B) for B in (8, 16)}
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).cuda(), 0, 255)
+    for ti in (0, 3, 7):
+        ot = ora.OTF(tfs[ti])
+        t = ess.ess_tf_set(ctx, torch.from_numpy(tfs[ti]).cuda())
+        xy = _pixels(W, H, 192, seed=ti)
+        ref, _ = ora.render_pixels(ov, ot, cams[ti], W, H, xy, dt=0.5, ert=0.99, threads=8)
+        for kind, B, params in ((ess.GRID, 8, {}), (ess.LBVH, 8, {}),
+                                (ess.KD, 8, dict(nbins=4, halting=1, mls=32)),
+                                (ess.HYBRID, 16, dict(nbins=4, halting=0))):
+            st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=B, rescan=1, **params))
+            ref_mask = ora.brick_mask(mm[B][0], mm[B][1], ot, 0, 255)
+            assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_MASK), ref_mask)
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+            ess.ess_render(ctx, st, cams[ti], ess.render_params(0.5, 0.99), W, H, out)
+            ess.ess_sync(ctx)
+            _check_pixels(out.cpu().numpy(), xy, ref, "ct512 TF %d %s" % (ti, ess.KIND_NAMES[kind]))
+            ess.ess_release(ctx, st)
+        ess.ess_release(ctx, t)
+
+
+def test_fractal1024_f32_mask_and_sampled_pixels(gpu, ctx, ora):
+    """The 1024^3 float32 fractal field (4 GiB) with a 1024-entry TF."""
+    ess, torch = gpu
+    dims = (1024, 1024, 1024)
+    x = synth.fractal_f32_torch(dims, seed=2, device="cuda")
+    host = x.cpu().numpy()
+    ov = ora.OVolume(host, 0.0, 1.0)
+    vol = ess.ess_volume_upload(ctx, x, 0.0, 1.0)
+    del x
+    tf_np = synth.tf_ramp(1024, 2)
+    ot = ora.OTF(tf_np)
+    t = ess.ess_tf_set(ctx, torch.from_numpy(tf_np).cuda())
+    mn, mx = ora.brick_minmax(ov, 8)
+    ref_mask = ora.brick_mask(mn, mx, ot, 0.0, 1.0)
+    W, H = 1920, 1080
+    cam = synth.orbit_camera(dims, W, H, theta=0.7, phi=0.35, dist=1.6)
+    xy = _pixels(W, H, 96, seed=5)
+    ref, _ = ora.render_pixels(ov, ot, cam, W, H, xy, dt=0.5, ert=0.99, threads=8)
+    for kind, params in ((ess.GRID, {}), (ess.LBVH, {}), (ess.KD, dict(nbins=4, halting=1, mls=32))):
+        st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=8, **params))
+        assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_MASK), ref_mask)
+        out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        ess.ess_render(ctx, st, cam, ess.render_params(0.5, 0.99), W, H, out)
+        ess.ess_sync(ctx)
+        _check_pixels(out.cpu().numpy(), xy, ref, "fractal1024 %s" % ess.KIND_NAMES[kind])
+        ess.ess_release(ctx, st)
