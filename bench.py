@@ -198,6 +198,24 @@ def dist_setup():
     return rank, local, ws, dist
 
 
+def max_over_ranks(dist, x, device):
+    """The largest of the ranks' values of x (each rank's timing): the job
+    is as slow as its slowest replica.  x itself when there is one rank."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, world_size, steps, ms):
+    """Whole-job throughput of `world_size` replicas that each process
+    `units_per_rank_step` units per step, over `steps` steps in `ms`
+    milliseconds (the max over ranks)."""
+    return world_size * units_per_rank_step * steps / (ms / 1000.0)
+
+
 # ---------------------------------------------------------------- reference
 def cpu_cores():
     try:
@@ -691,11 +709,7 @@ def run_ours(args, rank, local, ws, dist):
         ess.ess_profile_enable(ctx, False)
         prof = ess.ess_profile_read(ctx)
         ess.ess_sync(ctx)
-        t_ms = sum(a.elapsed_time(b) for a, b in ev)
-        if dist:
-            tt = torch.tensor([t_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_ms = float(tt.item())
+        t_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev), dev)
 
         # end to end through the ABI with host buffers
         for _ in range(max(1, args.warmup // 2)):
@@ -708,16 +722,12 @@ def run_ours(args, rank, local, ws, dist):
         for _ in range(args.steps):
             step(host_io=True)
         ess.ess_sync(ctx)
-        e2e_ms = 1000.0 * (time.perf_counter() - t0)
-        if dist:
-            tt = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt.item())
+        e2e_ms = max_over_ranks(dist, 1000.0 * (time.perf_counter() - t0), dev)
 
     units_step = sum(n_naive) * len(kinds)
     evaluated_step = sum(sum(v) for v in n_eval.values())
-    value = ws * units_step * args.steps / (t_ms / 1000.0)
-    e2e_value = ws * units_step * args.steps / (e2e_ms / 1000.0)
+    value = job_rate(units_step, ws, args.steps, t_ms)
+    e2e_value = job_rate(units_step, ws, args.steps, e2e_ms)
 
     # dominant kernel and its roofline on algorithmic bytes
     dom = max(prof.items(), key=lambda kv: kv[1][1])
@@ -796,7 +806,7 @@ def run_ours(args, rank, local, ws, dist):
                    "nonempty_brick_fraction": [round(x, 4) for x in nonempty],
                    "l2": "flushed between timed steps (%d MiB write, untimed)" % (L2_FLUSH_BYTES >> 20),
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "evaluated_samples_per_s": ws * evaluated_step * args.steps / (t_ms / 1000.0),
+        "evaluated_samples_per_s": job_rate(evaluated_step, ws, args.steps, t_ms),
         "samples_per_frame": {"naive_equivalent": float(np.mean(n_naive)),
                               **{ess.KIND_NAMES[k]: float(np.mean(v)) for k, v in n_eval.items()}},
         "ms_per_frame": per_frame,
