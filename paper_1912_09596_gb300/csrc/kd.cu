@@ -18,8 +18,9 @@
 // kernel accumulates the tight box of the bricks of every slab with integer
 // min/max atomics (order independent, hence deterministic), one kernel per
 // node turns slab boxes into the prefix/suffix unions that are the candidate
-// L and R boxes and picks the split, a scan numbers the children, and one
-// kernel emits them.  With an even nbins the middle plane lo + floor(e/2) is
+// L and R boxes and picks the split, and one kernel numbers and emits the
+// children (each block after the split counts of the blocks before it) and,
+// in its last block to finish, moves the level state on.  With an even nbins the middle plane lo + floor(e/2) is
 // candidate j = nbins/2, so a forced middle split also falls on a slab border.
 #include <cuda_runtime.h>
 
@@ -121,14 +122,15 @@ __device__ __forceinline__ bool slab_load(const int32_t *e, int32_t box[6])
 }
 
 // Level state, in device memory so that the level loop can run without the
-// host: the kernels of a level read it, the advance kernel moves it on.
+// host: the kernels of a level read it, the last emit block moves it on.
 struct KdState {
     int prev_begin;  // first node of the previous level
     int lvl_begin;   // first node of the current level
     int lvl_size;    // nodes on the current level (0: done)
     int levels;      // levels started so far; the current level is number `levels`
-    int splits;      // splits on the current level (from the scan)
-    int pad[3];
+    int splits;      // splits on the current level
+    unsigned done;   // emit blocks finished on the current level
+    int pad[2];
 };
 
 // Slab buffer of the current level (parity of the level number) and of the next.
@@ -152,6 +154,7 @@ __global__ void k_kd_root_init(int32_t *root_box, KdState *st)
         st->lvl_size = 1;
         st->levels = 0;
         st->splits = 0;
+        st->done = 0;
     }
 }
 
@@ -429,102 +432,91 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
     if (threadIdx.x == 0) block_sums[blockIdx.x] = (uint32_t)total;
 }
 
-// exclusive scan of the level's block split counts; total -> st->splits
-__global__ void __launch_bounds__(1024) k_kd_scan(uint32_t *block_sums, KdState *st)
+// Sum of v over the block (256 threads).
+__device__ __forceinline__ uint32_t kd_block_sum(uint32_t v)
 {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    const int nblk = (st->lvl_size + 255) / 256;
-    int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    if (t == 0) carry = 0;
+    __shared__ uint32_t part[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) part[w] = v;
     __syncthreads();
-    for (int base = 0; base < nblk; base += 1024) {
-        int i = base + t;
-        uint32_t v = i < nblk ? block_sums[i] : 0u;
-        uint32_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) wsum[w] = incl;
-        __syncthreads();
-        if (w == 0) {
-            uint32_t s = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            wsum[lane] = s;
-        }
-        __syncthreads();
-        uint32_t ex = carry + (w > 0 ? wsum[w - 1] : 0u) + incl - v;
-        if (i < nblk) block_sums[i] = ex;
-        __syncthreads();
-        if (t == 0) carry += wsum[31];
-        __syncthreads();
-    }
-    if (t == 0) st->splits = (int)carry;
+    uint32_t t = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += part[j];
+    __syncthreads();
+    return t;
 }
 
-// Writes split decisions into the node records and creates the children
-// (BFS numbering: after all nodes of this level, in node order, left first);
-// their slabs were zeroed by the decide kernel.
+// Emit and advance of one level.  Each block holding nodes of the level
+// numbers its split nodes after the splits of the blocks before it (the sum
+// of their counts from the decide step), writes the split decisions and the
+// two children of each split node; the last block to finish moves the level
+// state on (next level = the children, 2 x all splits) and, in the graph,
+// sets the loop condition.
 __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ dec,
-                                                 const uint32_t *__restrict__ block_off,
-                                                 int32_t *nodes9, int32_t *slabs0, int32_t *slabs1,
-                                                 int S, int capacity, uint32_t *status,
-                                                 const KdState *st)
+                                                 const uint32_t *__restrict__ block_counts,
+                                                 int32_t *nodes9, int capacity, int max_levels,
+                                                 uint32_t *status, KdState *st,
+                                                 cudaGraphConditionalHandle handle, int use_handle)
 {
     const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
-    if ((int)(blockIdx.x * blockDim.x) >= lvl_size) return;  // uniform per block
-    int l = blockIdx.x * blockDim.x + threadIdx.x;
-    int split = l < lvl_size ? dec[l].split : 0;
-    // block-local exclusive rank of the split flag
-    __shared__ uint32_t wcount[8];
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t ball = __ballot_sync(0xffffffffu, split);
-    if (lane == 0) wcount[w] = __popc(ball);
+    const int nblk = (lvl_size + 255) / 256;
+    if ((int)(blockIdx.x * blockDim.x) < lvl_size) {  // uniform per block
+        uint32_t off = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) off += block_counts[i];
+        off = kd_block_sum(off);
+        const int l = blockIdx.x * blockDim.x + threadIdx.x;
+        const int split = l < lvl_size ? dec[l].split : 0;
+        // block-local exclusive rank of the split flag
+        __shared__ uint32_t wcount[8];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        const uint32_t ball = __ballot_sync(0xffffffffu, split);
+        if (lane == 0) wcount[w] = __popc(ball);
+        __syncthreads();
+        uint32_t before = 0;
+        for (int j = 0; j < w; ++j) before += wcount[j];
+        if (split) {
+            const uint32_t rank = off + before + __popc(ball & ((1u << lane) - 1u));
+            const int fc = lvl_begin + lvl_size + 2 * (int)rank;
+            if (fc + 1 >= capacity) {
+                atomicOr(status, DEV_ERR_OVERFLOW);
+            } else {
+                const KdDecision &d = dec[l];
+                int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + l);
+                rec[6] = d.axis;
+                rec[7] = d.plane;
+                rec[8] = fc;
+                int32_t *cl = nodes9 + 9 * (size_t)fc;
+                int32_t *cr = cl + 9;
+                for (int k = 0; k < 6; ++k) {
+                    cl[k] = d.L[k];
+                    cr[k] = d.R[k];
+                }
+                cl[6] = cr[6] = -1;
+                cl[7] = cr[7] = 0;
+                cl[8] = cr[8] = -1;
+            }
+        }
+    }
+    // the last block to finish advances the level
+    __shared__ bool last;
     __syncthreads();
-    uint32_t before = 0;
-    for (int j = 0; j < w; ++j) before += wcount[j];
-    if (!split) return;
-    uint32_t rank = block_off[blockIdx.x] + before + __popc(ball & ((1u << lane) - 1u));
-    int lvl_end = lvl_begin + lvl_size;
-    int fc = lvl_end + 2 * (int)rank;
-    if (fc + 1 >= capacity) {
-        atomicOr(status, DEV_ERR_OVERFLOW);
-        return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
     }
-    const KdDecision &d = dec[l];
-    int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + l);
-    rec[6] = d.axis;
-    rec[7] = d.plane;
-    rec[8] = fc;
-    int32_t *cl = nodes9 + 9 * (size_t)fc;
-    int32_t *cr = cl + 9;
-    for (int k = 0; k < 6; ++k) {
-        cl[k] = d.L[k];
-        cr[k] = d.R[k];
-    }
-    cl[6] = cr[6] = -1;
-    cl[7] = cr[7] = 0;
-    cl[8] = cr[8] = -1;
-}
-
-// Moves the level state on; in the graph build it also decides on the device
-// whether the level loop continues.  A tree that would exceed the node
-// capacity or the renderer's depth limit stops with DEV_ERR_OVERFLOW.
-__global__ void k_kd_advance(KdState *st, int capacity, int max_levels, uint32_t *status,
-                             cudaGraphConditionalHandle handle, int use_handle)
-{
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    uint32_t total = 0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) total += block_counts[i];
+    total = kd_block_sum(total);
     if (threadIdx.x != 0) return;
-    int size = st->lvl_size;
-    if (size > 0) {
-        int next = 2 * st->splits;
-        st->prev_begin = st->lvl_begin;
-        st->lvl_begin += size;
+    st->done = 0;
+    if (lvl_size > 0) {
+        int next = 2 * (int)total;
+        st->prev_begin = lvl_begin;
+        st->lvl_begin = lvl_begin + lvl_size;
         st->levels += 1;
         if (next > 0 && (st->lvl_begin + next > capacity || st->levels >= max_levels)) {
             atomicOr(status, DEV_ERR_OVERFLOW);
@@ -535,6 +527,7 @@ __global__ void k_kd_advance(KdState *st, int capacity, int max_levels, uint32_t
     }
     if (use_handle) cudaGraphSetConditional(handle, st->lvl_size > 0 ? 1u : 0u);
 }
+
 
 // Traversal layout: one BoxNode per node id (leaf entries unused), children
 // referenced as node ids, leaves as -1 - id; the root record and node count.
@@ -643,7 +636,7 @@ static void kd_root_launches(Ctx &c, Structure &s, const KdParams &P, unsigned b
                                        st);
 }
 
-// One level: accumulate, decide, scan, emit, advance.
+// One level: accumulate, decide, emit (which also advances the level state).
 static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks,
                               unsigned node_blocks, int next_cap, cudaGraphConditionalHandle h,
                               int use_handle)
@@ -659,12 +652,9 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
         k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
                                                           s.kd_vr, (KdDecision *)s.kd_dec,
                                                           s.kd_block_sums, st, P, next_cap);
-    k_kd_scan<<<1, 1024, 0, c.stream>>>(s.kd_block_sums, st);
     k_kd_emit<<<node_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
-                                                 s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], P.S,
-                                                 s.kd_capacity, c.dev_status, st);
-    k_kd_advance<<<1, 32, 0, c.stream>>>(st, s.kd_capacity, KD_MAX_LEVELS, c.dev_status, h,
-                                         use_handle);
+                                                 s.kd_nodes, s.kd_capacity, KD_MAX_LEVELS,
+                                                 c.dev_status, st, h, use_handle);
 }
 
 // Whether the whole build runs as one device-driven graph: binned planes and
