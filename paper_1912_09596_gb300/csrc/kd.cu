@@ -432,6 +432,146 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
     if (threadIdx.x == 0) block_sums[blockIdx.x] = (uint32_t)total;
 }
 
+// Warp-parallel decide for 4 bins (4 slabs per axis): half a warp per node,
+// lane (a, j) = (axis, slab) for the first 12 lanes.  The slab boxes' prefix
+// unions (slabs before j: the L box of plane j) and suffix unions (slabs j
+// onwards: the R box) come from shuffles within each axis's 4 lanes; the
+// candidate of lane (a, j), 1 <= j < ns, costs V(L) + V(R), and the argmin
+// over the half takes the lowest (axis, plane) among equal costs, as the
+// per-thread form does.  Integer arithmetic only, so the decisions are the
+// same.  Split counts per 256 nodes are added atomically (the emit kernel's
+// last block zeroes them for the next level).
+__device__ __forceinline__ bool box_nonempty(const int32_t *b) { return b[0] != INT_MAX; }
+
+__global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ nodes9,
+                                                    int32_t *slabs0, int32_t *slabs1, KdDecision *dec,
+                                                    uint32_t *block_counts, const KdState *st,
+                                                    KdParams P, int next_cap)
+{
+    constexpr int S = 4;
+    const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if (lvl_size <= 0) return;  // uniform
+    {
+        // the next level has at most min(2 lvl_size, capacity) nodes
+        int2 *next = reinterpret_cast<int2 *>(kd_next_slabs(slabs0, slabs1, st));
+        const size_t words = (size_t)min(2 * lvl_size, next_cap) * 9 * S;  // 18 S ints per node
+        const size_t stride = (size_t)gridDim.x * blockDim.x;
+        for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < words; q += stride)
+            next[q] = make_int2(0, 0);
+    }
+    const int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
+    const unsigned long long Vroot = kd_volume(nodes9, P);
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+    const int a = (hl >> 2) < 3 ? hl >> 2 : 0, j = hl & 3;
+    const bool slab_lane = hl < 12;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    for (int base = 2 * gw; base < lvl_size; base += 2 * warps) {  // uniform per warp
+        const int l = base + half;
+        const bool node = l < lvl_size;
+        const int32_t *X = nodes9 + 9 * (size_t)(lvl_begin + (node ? l : 0));
+        int32_t x[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] = X[k];
+        const unsigned long long V = kd_volume(x, P);
+        const bool allowed = node && (P.halting == 0 ? (10ull * V > Vroot) : (V > 512ull));
+        const int lo = x[a], hi = x[3 + a];
+        const bool axis_ok = slab_lane && hi - lo >= 2;
+        const int ns = axis_ok ? kd_slabs(lo, hi, P.nbins) : 0;
+        int32_t b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+        if (allowed && axis_ok && j < ns) {
+            int32_t t[6];
+            if (slab_load(slabs + 6 * (((size_t)l * 3 + a) * S + j), t)) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) b[k] = t[k];
+            }
+        }
+        // inclusive prefix and suffix unions over the axis's 4 lanes
+        int32_t pre[6], suf[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pre[k] = suf[k] = b[k];
+#pragma unroll
+        for (int d = 1; d < 4; d <<= 1) {
+            int32_t up[6], dn[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                up[k] = __shfl_up_sync(0xffffffffu, pre[k], d, 4);
+                dn[k] = __shfl_down_sync(0xffffffffu, suf[k], d, 4);
+            }
+            if (j >= d) box_union(pre, up);
+            if (j + d < 4) box_union(suf, dn);
+        }
+        int32_t L[6];  // slabs before j: exclusive prefix
+#pragma unroll
+        for (int k = 0; k < 6; ++k) L[k] = __shfl_up_sync(0xffffffffu, pre[k], 1, 4);
+        if (j == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) L[k] = INT_MAX, L[3 + k] = INT_MIN;
+        }
+        unsigned long long cost = ~0ull;
+        if (allowed && axis_ok && j >= 1 && j < ns && box_nonempty(L) && box_nonempty(suf))
+            cost = kd_volume(L, P) + kd_volume(suf, P);
+        // argmin over the half: (cost, lane) in lexicographic order
+        unsigned long long bc = cost;
+        int bl = hl;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            const unsigned long long oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (oc < bc || (oc == bc && ol < bl)) {
+                bc = oc;
+                bl = ol;
+            }
+        }
+        int bax = -1, bj = 0, bpl = 0;
+        if (allowed && bc != ~0ull && bc < V) {
+            bax = bl >> 2;
+            bj = bl & 3;
+            bpl = kd_plane(bj, x[bax], x[3 + bax], P.nbins);
+        } else if (allowed && P.mls3 > 0 && V > P.mls3) {
+            int bestext = -1;
+            const int n[3] = {P.nx, P.ny, P.nz};
+            for (int ax = 0; ax < 3; ++ax) {
+                const int e = x[3 + ax] - x[ax];
+                if (e < 2) continue;
+                const int ext = min(x[3 + ax] * P.B, n[ax]) - x[ax] * P.B;
+                if (ext > bestext) {
+                    bestext = ext;
+                    bax = ax;
+                    bpl = x[ax] + e / 2;
+                }
+            }
+            if (bax >= 0) bj = kd_slab_of(bpl, x[bax], x[3 + bax], P.nbins);
+        }
+        // the L and R boxes of the chosen plane are lane (bax, bj)'s
+        const int src = (half << 4) + (bax >= 0 ? bax * 4 + bj : 0);
+        int32_t dl[6], dr[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            dl[k] = __shfl_sync(0xffffffffu, L[k], src);
+            dr[k] = __shfl_sync(0xffffffffu, suf[k], src);
+        }
+        if (hl == 0 && node) {
+            KdDecision d;
+            d.split = 0;
+            d.axis = -1;
+            d.plane = 0;
+            if (bax >= 0 && box_nonempty(dl) && box_nonempty(dr)) {
+                d.split = 1;
+                d.axis = bax;
+                d.plane = bpl;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    d.L[k] = dl[k];
+                    d.R[k] = dr[k];
+                }
+                atomicAdd(block_counts + (l >> 8), 1u);
+            }
+            dec[l] = d;
+        }
+    }
+}
+
 // Sum of v over the block (256 threads).
 __device__ __forceinline__ uint32_t kd_block_sum(uint32_t v)
 {
@@ -454,7 +594,7 @@ __device__ __forceinline__ uint32_t kd_block_sum(uint32_t v)
 // state on (next level = the children, 2 x all splits) and, in the graph,
 // sets the loop condition.
 __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ dec,
-                                                 const uint32_t *__restrict__ block_counts,
+                                                 uint32_t *block_counts,
                                                  int32_t *nodes9, int capacity, int max_levels,
                                                  uint32_t *status, KdState *st,
                                                  cudaGraphConditionalHandle handle, int use_handle)
@@ -511,6 +651,7 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
     uint32_t total = 0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) total += block_counts[i];
     total = kd_block_sum(total);
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) block_counts[i] = 0;  // for the next level
     if (threadIdx.x != 0) return;
     st->done = 0;
     if (lvl_size > 0) {
@@ -606,8 +747,13 @@ void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur)
     s.kd_vr = (unsigned long long *)vr;
     grow(c, s.kd_dec, s.kd_dec_cap, (size_t)lvl_size, sizeof(KdDecision));
     void *bs = s.kd_block_sums;
+    const size_t bs_cap = s.kd_bs_cap;
     grow(c, bs, s.kd_bs_cap, (size_t)(lvl_size + 255) / 256, sizeof(uint32_t));
     s.kd_block_sums = (uint32_t *)bs;
+    // the split counts start from zero (a new buffer; the emit kernel zeroes
+    // them after each level)
+    if (s.kd_bs_cap != bs_cap)
+        ESS_CUDA(cudaMemsetAsync(s.kd_block_sums, 0, sizeof(uint32_t) * s.kd_bs_cap, c.stream));
 }
 
 void kd_free(Ctx &c, Structure &s)
@@ -629,6 +775,8 @@ void kd_free(Ctx &c, Structure &s)
 static void kd_root_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks)
 {
     KdState *st = (KdState *)s.kd_state;
+    if (s.kd_block_sums)  // per-level split counts start from zero
+        ESS_CUDA(cudaMemsetAsync(s.kd_block_sums, 0, sizeof(uint32_t) * s.kd_bs_cap, c.stream));
     k_kd_root_init<<<1, 32, 0, c.stream>>>(s.kd_scratch_i32, st);
     k_kd_root_reduce<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.gx, s.gy,
                                                          s.kd_scratch_i32);
@@ -645,9 +793,9 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
     k_kd_accumulate<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node, s.kd_nodes,
                                                         s.kd_slabs[0], s.kd_slabs[1], st, P);
     if (P.S == 4)
-        k_kd_decide<4><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
-                                                          s.kd_vr, (KdDecision *)s.kd_dec,
-                                                          s.kd_block_sums, st, P, next_cap);
+        k_kd_decide4<<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
+                                                        (KdDecision *)s.kd_dec, s.kd_block_sums, st,
+                                                        P, next_cap);
     else
         k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
                                                           s.kd_vr, (KdDecision *)s.kd_dec,
