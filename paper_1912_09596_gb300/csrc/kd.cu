@@ -218,6 +218,8 @@ __device__ __forceinline__ void slab_atomic(int32_t *slot, const int v[6])
     for (int k = 0; k < 6; ++k) atomicMax(slot + k, v[k]);
 }
 
+// NBINS > 0: the bin count known at compile time (divisions become shifts).
+template <int NBINS>
 __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restrict__ ids,
                                                        const int *__restrict__ count,
                                                        int *__restrict__ brick_node,
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         bool use = live && box[3 + a] - box[a] >= 2;
-        int s = use ? kd_slab_of(c[a], box[a], box[3 + a], P.nbins) : 0;
+        int s = use ? kd_slab_of(c[a], box[a], box[3 + a], NBINS > 0 ? NBINS : P.nbins) : 0;
         long long slot_id = use ? ((long long)local * 3 + a) * P.S + s : -1;
         long long first = __shfl_sync(0xffffffffu, slot_id, 0);
         if (__all_sync(0xffffffffu, slot_id == first)) {
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
         const bool allowed = node && (P.halting == 0 ? (10ull * V > Vroot) : (V > 512ull));
         const int lo = x[a], hi = x[3 + a];
         const bool axis_ok = slab_lane && hi - lo >= 2;
-        const int ns = axis_ok ? kd_slabs(lo, hi, P.nbins) : 0;
+        const int ns = axis_ok ? kd_slabs(lo, hi, 4) : 0;
         int32_t b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
         if (allowed && axis_ok && j < ns) {
             int32_t t[6];
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
         if (allowed && bc != ~0ull && bc < V) {
             bax = bl >> 2;
             bj = bl & 3;
-            bpl = kd_plane(bj, x[bax], x[3 + bax], P.nbins);
+            bpl = kd_plane(bj, x[bax], x[3 + bax], 4);
         } else if (allowed && P.mls3 > 0 && V > P.mls3) {
             int bestext = -1;
             const int n[3] = {P.nx, P.ny, P.nz};
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
                     bpl = x[ax] + e / 2;
                 }
             }
-            if (bax >= 0) bj = kd_slab_of(bpl, x[bax], x[3 + bax], P.nbins);
+            if (bax >= 0) bj = kd_slab_of(bpl, x[bax], x[3 + bax], 4);
         }
         // the L and R boxes of the chosen plane are lane (bax, bj)'s
         const int src = (half << 4) + (bax >= 0 ? bax * 4 + bj : 0);
@@ -790,8 +792,14 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
                               int use_handle)
 {
     KdState *st = (KdState *)s.kd_state;
-    k_kd_accumulate<<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node, s.kd_nodes,
-                                                        s.kd_slabs[0], s.kd_slabs[1], st, P);
+    if (P.nbins == 4)
+        k_kd_accumulate<4><<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node,
+                                                               s.kd_nodes, s.kd_slabs[0],
+                                                               s.kd_slabs[1], st, P);
+    else
+        k_kd_accumulate<0><<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node,
+                                                               s.kd_nodes, s.kd_slabs[0],
+                                                               s.kd_slabs[1], st, P);
     if (P.S == 4)
         k_kd_decide4<<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
                                                         (KdDecision *)s.kd_dec, s.kd_block_sums, st,
