@@ -569,6 +569,52 @@ def run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, steps=3):
             "workload": "the main workload's 8 TF edits, one rebuild and one frame each", **res}
 
 
+def run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, reps=3):
+    """Table 1 / Table 2 style comparison on the main workload (Sec. 4.3): node
+    count, height, build time and frame time of the LBVH and of the k-d tree
+    built shallow, deep, deep with MLS 32 and MLS 128 (binned planes, 4 bins, as
+    the GPU builder of the paper, and exhaustive brick-boundary planes), plus
+    the grid and the hybrid grid, for the sparsest and the densest TF edit."""
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    configs = [("grid", ess.GRID, {}), ("lbvh", ess.LBVH, {}), ("hybrid", ess.HYBRID, dict(halting=0))]
+    for nb in (4, 0):
+        for name, prm in (("shallow", dict(halting=0)), ("deep", dict(halting=1)),
+                          ("deep_mls32", dict(halting=1, mls=32)), ("deep_mls128", dict(halting=1, mls=128))):
+            configs.append(("kd_%s_%s" % ("binned" if nb else "exhaustive", name), ess.KD, dict(nbins=nb, **prm)))
+    nonempty = []
+    for i in range(len(tf_dev)):
+        ess.ess_tf_update(ctx, tf, tf_dev[i])
+        g = ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=8))
+        nonempty.append(ess.ess_structure_info_get(ctx, g)["n_nonempty"])
+        ess.ess_release(ctx, g)
+    picks = sorted({int(np.argmin(nonempty)), int(np.argmax(nonempty))})
+    rows = []
+    for i in picks:
+        ess.ess_tf_update(ctx, tf, tf_dev[i])
+        for name, kind, prm in configs:
+            st = ess.ess_build(ctx, vol, tf, kind, ess.build_params(brick=8, **prm))
+            ess.ess_render(ctx, st, ecams[i], rp, W, H, out)   # warm
+            ess.ess_sync(ctx)
+            ess.ess_profile_reset(ctx)
+            ess.ess_profile_enable(ctx, True)
+            for _ in range(reps):
+                ess.ess_rebuild(ctx, st)
+                ess.ess_render(ctx, st, ecams[i], rp, W, H, out)
+            ess.ess_sync(ctx)
+            ess.ess_profile_enable(ctx, False)
+            prof = ess.ess_profile_read(ctx)
+            info = ess.ess_structure_info_get(ctx, st)
+            render = sum(v[1] for k, v in prof.items() if k.startswith("render")) / reps
+            build = sum(v[1] for k, v in prof.items() if not k.startswith("render")) / reps
+            rows.append({"tf_edit": i, "nonempty_bricks": int(nonempty[i]), "structure": name,
+                         "nodes": int(info["n_nodes"]), "height": int(info["height"]),
+                         "build_ms": round(build, 4), "frame_ms": round(render, 4)})
+            ess.ess_release(ctx, st)
+    return {"workload": "the main workload (512^3 CT-like, 8^3 bricks, 1024^2 frame), sparsest and "
+                        "densest of its TF edits; build = one rebuild (min/max cached), frame = one "
+                        "render, CUDA-event means of %d" % reps, "rows": rows}
+
+
 def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
     """The per-brick min/max pass (rebuild with rescan) over larger volumes and
     every dtype: device time per launch with L2 flushed before each, against
@@ -824,6 +870,10 @@ def run_ours(args, rank, local, ws, dist):
     if not args.no_hybrid:
         with torch.cuda.stream(stream):
             result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
+    if not args.no_structures:
+        with torch.cuda.stream(stream):
+            result["structures"] = run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams,
+                                                  rp, W, H)
     if not args.no_batched:
         with torch.cuda.stream(stream):
             result["batched"] = run_batched(ess, torch, dev, stream, ctx)
@@ -862,6 +912,8 @@ def main():
                     help="skip the brick min/max sweep over dtypes and sizes")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the hybrid-grid leg")
+    ap.add_argument("--no-structures", action="store_true",
+                    help="skip the structure comparison (node counts, heights, build and frame times)")
     args = ap.parse_args()
     rank, local, ws, dist = dist_setup()
     if args.impl == "reference":
