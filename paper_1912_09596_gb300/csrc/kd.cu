@@ -237,54 +237,56 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
         for (int k = 0; k < 6; ++k) s_val[h][k] = 0;
     }
     __syncthreads();
-    int n = *count;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool live = i < n;
-    int c[3] = {0, 0, 0};
-    int node = -1;
-    if (live) {
-        brick_coords(ids[i], P.gx, P.gy, c);
-        node = lvl_begin == 0 ? 0 : brick_node[i];
-        if (node >= prev_begin && node < lvl_begin) {
-            const int32_t *rec = nodes9 + 9 * (size_t)node;
-            int fc = rec[8];
-            if (fc >= 0) {
-                node = fc + (c[rec[6]] >= rec[7] ? 1 : 0);
-                brick_node[i] = node;
-            }
-        } else if (lvl_begin == 0) {
-            brick_node[i] = 0;
-        }
-        if (node < lvl_begin || node >= lvl_begin + lvl_size) live = false;
-    }
-    const int32_t *box = nodes9 + 9 * (size_t)(live ? node : 0);
-    int local = node - lvl_begin;
-    const int v[6] = {KD_LO_BIAS - c[0], KD_LO_BIAS - c[1], KD_LO_BIAS - c[2],
-                      c[0] + 1, c[1] + 1, c[2] + 1};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        bool use = live && box[3 + a] - box[a] >= 2;
-        int s = use ? kd_slab_of(c[a], box[a], box[3 + a], NBINS > 0 ? NBINS : P.nbins) : 0;
-        long long slot_id = use ? ((long long)local * 3 + a) * P.S + s : -1;
-        long long first = __shfl_sync(0xffffffffu, slot_id, 0);
-        if (__all_sync(0xffffffffu, slot_id == first)) {
-            if (first < 0) continue;
-            int r[6];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) r[k] = __reduce_max_sync(0xffffffffu, v[k]);
-            if ((threadIdx.x & 31) == 0) slab_atomic(slabs + 6 * first, r);
-        } else if (use) {
-            int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> 57);  // 7 bits
-            bool done = false;
-            for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (KD_HT - 1)) {
-                long long old = atomicCAS((unsigned long long *)&s_key[h], (unsigned long long)-1ll,
-                                          (unsigned long long)slot_id);
-                if (old == -1 || old == slot_id) {
-                    for (int k = 0; k < 6; ++k) atomicMax(&s_val[h][k], v[k]);
-                    done = true;
+    const int n = *count;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;  // the loop is uniform per block
+        bool live = i < n;
+        int c[3] = {0, 0, 0};
+        int node = -1;
+        if (live) {
+            brick_coords(ids[i], P.gx, P.gy, c);
+            node = lvl_begin == 0 ? 0 : brick_node[i];
+            if (node >= prev_begin && node < lvl_begin) {
+                const int32_t *rec = nodes9 + 9 * (size_t)node;
+                int fc = rec[8];
+                if (fc >= 0) {
+                    node = fc + (c[rec[6]] >= rec[7] ? 1 : 0);
+                    brick_node[i] = node;
                 }
+            } else if (lvl_begin == 0) {
+                brick_node[i] = 0;
             }
-            if (!done) slab_atomic(slabs + 6 * slot_id, v);
+            if (node < lvl_begin || node >= lvl_begin + lvl_size) live = false;
+        }
+        const int32_t *box = nodes9 + 9 * (size_t)(live ? node : 0);
+        int local = node - lvl_begin;
+        const int v[6] = {KD_LO_BIAS - c[0], KD_LO_BIAS - c[1], KD_LO_BIAS - c[2],
+                          c[0] + 1, c[1] + 1, c[2] + 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bool use = live && box[3 + a] - box[a] >= 2;
+            int s = use ? kd_slab_of(c[a], box[a], box[3 + a], NBINS > 0 ? NBINS : P.nbins) : 0;
+            long long slot_id = use ? ((long long)local * 3 + a) * P.S + s : -1;
+            long long first = __shfl_sync(0xffffffffu, slot_id, 0);
+            if (__all_sync(0xffffffffu, slot_id == first)) {
+                if (first < 0) continue;
+                int r[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) r[k] = __reduce_max_sync(0xffffffffu, v[k]);
+                if ((threadIdx.x & 31) == 0) slab_atomic(slabs + 6 * first, r);
+            } else if (use) {
+                int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> 57);  // 7 bits
+                bool done = false;
+                for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (KD_HT - 1)) {
+                    long long old = atomicCAS((unsigned long long *)&s_key[h], (unsigned long long)-1ll,
+                                              (unsigned long long)slot_id);
+                    if (old == -1 || old == slot_id) {
+                        for (int k = 0; k < 6; ++k) atomicMax(&s_val[h][k], v[k]);
+                        done = true;
+                    }
+                }
+                if (!done) slab_atomic(slabs + 6 * slot_id, v);
+            }
         }
     }
     __syncthreads();
@@ -603,11 +605,11 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
 {
     const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
     const int nblk = (lvl_size + 255) / 256;
-    if ((int)(blockIdx.x * blockDim.x) < lvl_size) {  // uniform per block
+    for (int gb = blockIdx.x; gb < nblk; gb += gridDim.x) {  // uniform per block
         uint32_t off = 0;
-        for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) off += block_counts[i];
+        for (int i = threadIdx.x; i < gb; i += blockDim.x) off += block_counts[i];
         off = kd_block_sum(off);
-        const int l = blockIdx.x * blockDim.x + threadIdx.x;
+        const int l = gb * blockDim.x + threadIdx.x;
         const int split = l < lvl_size ? dec[l].split : 0;
         // block-local exclusive rank of the split flag
         __shared__ uint32_t wcount[8];
@@ -639,6 +641,7 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
                 cl[8] = cr[8] = -1;
             }
         }
+        __syncthreads();  // wcount is rewritten by the next group
     }
     // the last block to finish advances the level
     __shared__ bool last;
@@ -788,8 +791,8 @@ static void kd_root_launches(Ctx &c, Structure &s, const KdParams &P, unsigned b
 
 // One level: accumulate, decide, emit (which also advances the level state).
 static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned brick_blocks,
-                              unsigned node_blocks, int next_cap, cudaGraphConditionalHandle h,
-                              int use_handle)
+                              unsigned node_blocks, unsigned emit_blocks, int next_cap,
+                              cudaGraphConditionalHandle h, int use_handle)
 {
     KdState *st = (KdState *)s.kd_state;
     if (P.nbins == 4)
@@ -808,7 +811,7 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
         k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
                                                           s.kd_vr, (KdDecision *)s.kd_dec,
                                                           s.kd_block_sums, st, P, next_cap);
-    k_kd_emit<<<node_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
+    k_kd_emit<<<emit_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
                                                  s.kd_nodes, s.kd_capacity, KD_MAX_LEVELS,
                                                  c.dev_status, st, h, use_handle);
 }
@@ -832,6 +835,13 @@ static bool kd_graph_fits(const Structure &s, int S)
     return bytes < free_b / 8;
 }
 
+// Levels per iteration of the graph's while loop.  Each iteration of a
+// conditional node costs far more than a kernel node, so the body holds several
+// levels; a level after the last one finds an empty level state and returns at
+// once (all three kernels), and the emit kernel of every level sets the loop
+// condition.
+constexpr int KD_LEVELS_PER_ITERATION = 4;
+
 static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
 {
     size_t cap = (size_t)s.nb;
@@ -851,8 +861,15 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
     if (!c.capture_stream)
         ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
 
+    // The level kernels loop over their work, so their grids are sized for the
+    // machine (a few blocks per SM) rather than for the widest possible level,
+    // except the one-thread-per-node decide step of other bin counts.
     const unsigned brick_blocks = (unsigned)((cap + 255) / 256);
-    const unsigned node_blocks = brick_blocks;
+    int sms = 0;
+    ESS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    const unsigned acc_blocks = std::min(brick_blocks, 4u * (unsigned)sms);
+    const unsigned emit_blocks = std::min(brick_blocks, 2u * (unsigned)sms);
+    const unsigned node_blocks = P.S == 4 ? emit_blocks : brick_blocks;
     cudaGraph_t g;
     ESS_CUDA(cudaGraphCreate(&g, 0));
     cudaStream_t saved = c.stream;
@@ -881,8 +898,9 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
-        kd_level_launches(c, s, P, brick_blocks, node_blocks,
-                          (int)std::min(s.kd_slab_cap[0], s.kd_slab_cap[1]), h, 1);
+        for (int u = 0; u < KD_LEVELS_PER_ITERATION; ++u)
+            kd_level_launches(c, s, P, acc_blocks, node_blocks, emit_blocks,
+                              (int)std::min(s.kd_slab_cap[0], s.kd_slab_cap[1]), h, 1);
         ESS_CUDA(cudaStreamEndCapture(c.stream, &body));
         // traversal layout after the loop
         ESS_CUDA(cudaStreamBeginCaptureToGraph(c.stream, g, &loop, nullptr, 1,
@@ -939,7 +957,7 @@ void launch_kd(Ctx &c, Structure &s)
         unsigned nblk = (unsigned)((lvl_size + 255) / 256);
         {
             Launch L(c, "kd_level");
-            kd_level_launches(c, s, P, brick_blocks, nblk, (int)s.kd_slab_cap[cur ^ 1], 0, 0);
+            kd_level_launches(c, s, P, brick_blocks, nblk, nblk, (int)s.kd_slab_cap[cur ^ 1], 0, 0);
         }
         ESS_CUDA(cudaMemcpyAsync(&hs, s.kd_state, sizeof(KdState), cudaMemcpyDeviceToHost,
                                  c.stream));
