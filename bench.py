@@ -726,10 +726,13 @@ def run_ours(args, rank, local, ws, dist):
         ess.ess_sync(ctx)
 
         def step(host_io=False):
+            # the library runs the rebuilds on its build stream: the k-d and LBVH
+            # rebuilds overlap the grid's frame
             for i in range(len(tfs_np)):
                 ess.ess_tf_update(ctx, tf, tf_host[i] if host_io else tf_dev[i])
                 for k in kinds:
                     ess.ess_rebuild(ctx, st[k])
+                for k in kinds:
                     ess.ess_render(ctx, st[k], ecams[i], rp, W, H, host_out if host_io else outs[k])
 
         for _ in range(args.warmup):
@@ -775,11 +778,13 @@ def run_ours(args, rank, local, ws, dist):
     value = job_rate(units_step, ws, args.steps, t_ms)
     e2e_value = job_rate(units_step, ws, args.steps, e2e_ms)
 
-    # dominant kernel and its roofline on algorithmic bytes
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    # dominant kernel and its roofline on algorithmic bytes (among the renders:
+    # the build kernels run on the build stream alongside them, so their event
+    # intervals include the time they share the GPU with a render)
+    kind_of = {"render_grid": ess.GRID, "render_lbvh": ess.LBVH, "render_kd": ess.KD}
+    dom = max(((k, v) for k, v in prof.items() if k in kind_of), key=lambda kv: kv[1][1])
     dom_name, (dom_launches, dom_ms) = dom
     avg_ms = dom_ms / max(1, dom_launches)
-    kind_of = {"render_grid": ess.GRID, "render_lbvh": ess.LBVH, "render_kd": ess.KD}
     peak, peak_src = measured_peaks()
     if dom_name in kind_of and kind_of[dom_name] in alg_bytes:
         bytes_per_launch = float(np.mean(alg_bytes[kind_of[dom_name]]))
@@ -839,6 +844,9 @@ def run_ours(args, rank, local, ws, dist):
     total_build_ms = sum(v[1] for v in build_kernels.values())
     edits = args.steps * len(tfs_np)
     build_ms["all_structures_per_edit"] = total_build_ms / edits
+    build_ms["note"] = ("event intervals of the build kernels on the library's build stream, which "
+                        "run while the frames of the same edit render; the structures object "
+                        "times each build alone")
 
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,

@@ -24,7 +24,13 @@
  *  - Device memory that the library allocates belongs to the context and is
  *    returned by ess_release() / ess_destroy().
  *  - Work is issued asynchronously on the context's CUDA stream, in call
- *    order.  ess_sync() waits for it and reports device-side errors.
+ *    order, except builds and rebuilds: they run on an internal stream of the
+ *    highest priority, each after the last render of its structure and the
+ *    last updates of its TF and volume, so that a rebuild overlaps the
+ *    rendering of other structures.  Every later call that uses the structure
+ *    (render, batched render, read, info, release) and every TF update waits
+ *    for them on the context stream, so results are those of call order.
+ *    ess_sync() waits for all of it and reports device-side errors.
  *  - A context is used by one host thread at a time.
  *  - World units are voxels: the volume box is [0,nx] x [0,ny] x [0,nz] and
  *    voxel (i,j,k) has its centre at (i+0.5, j+0.5, k+0.5).
@@ -151,9 +157,10 @@ typedef struct {
  * (Sec. 3).  For ESS_NONE no index is built; the handle just binds the
  * volume and the TF for naive rendering.  ESS_HYBRID runs the k-d build with
  * `params` and keeps the brick mask as its global grid.  The structure keeps references to
- * `vol` and `tf`.  Asynchronous except for the k-d build, which reads back
- * one node count per tree level.  Errors: ESS_ERR_ARG for bad parameters,
- * ESS_ERR_HANDLE for bad handles, ESS_ERR_OOM. */
+ * `vol` and `tf`.  Asynchronous, except the k-d build with exhaustive planes
+ * (nbins 0), which reads back the size of each tree level.  Errors:
+ * ESS_ERR_ARG for bad parameters, ESS_ERR_HANDLE for bad handles,
+ * ESS_ERR_OOM. */
 ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
                      const ess_build_params *params, ess_handle *structure);
 

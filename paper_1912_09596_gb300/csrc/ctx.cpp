@@ -69,6 +69,31 @@ void Ctx::end()
     current = nullptr;
 }
 
+void mark(Ctx &c, cudaEvent_t &e)
+{
+    if (!e) ESS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ESS_CUDA(cudaEventRecord(e, c.stream));
+}
+
+// The context stream waits for the structure's last build.
+void join_build(Ctx &c, Structure &s)
+{
+    if (!s.build_pending) return;
+    ESS_CUDA(cudaStreamWaitEvent(c.stream, s.built, 0));
+    s.build_pending = false;
+}
+
+// The context stream waits for every build enqueued so far (before writing
+// what builds read: TF tables, the cell copy; and before reading the status
+// word or profiling events).
+void join_all_builds(Ctx &c)
+{
+    if (!c.build_stream) return;
+    ESS_CUDA(cudaEventRecord(c.fork_event, c.build_stream));
+    ESS_CUDA(cudaStreamWaitEvent(c.stream, c.fork_event, 0));
+    for (auto &kv : c.structures) kv.second->build_pending = false;
+}
+
 }  // namespace ess
 
 using namespace ess;
@@ -128,6 +153,7 @@ size_t dtype_size(ess_dtype d) { return d == ESS_U8 ? 1 : (d == ESS_U16 ? 2 : 4)
 // Reads and clears the device status word (synchronises the stream).
 ess_status take_status(Ctx &c, std::string &msg)
 {
+    join_all_builds(c);
     ESS_CUDA(cudaMemcpyAsync(c.host_status, c.dev_status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                              c.stream));
     ESS_CUDA(cudaStreamSynchronize(c.stream));
@@ -185,6 +211,7 @@ void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
     ESS_CUDA(cudaMemcpyAsync(t.table + t.nt, t.table + (t.nt - 1), sizeof(float4),
                              cudaMemcpyDeviceToDevice, c.stream));
     launch_tf_prefix(c, t.table, t.nt, t.prefix, on_device);
+    mark(c, t.updated);
     ++t.version;
 }
 
@@ -224,12 +251,16 @@ float2 *minmax_for(Ctx &c, Volume &v, int B, bool rescan)
 
 void free_structure(Ctx &c, Structure &s)
 {
+    join_build(c, s);
     void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_sorted, s.ids_sorted,
                     s.keys_alt, s.ids_alt, s.sort_scratch, s.left, s.right, s.parent,
                     s.leaf_parent, s.inner_box, s.inner_cnt, s.arrive, s.nodes, s.root, s.kd_nodes,
                     s.kd_count_dev, s.brick_node, s.kd_scratch_i32, s.kd_state};
     for (void *p : ptrs) c.free(p);
     kd_free(c, s);
+    if (s.built) cudaEventDestroy(s.built);
+    if (s.used) cudaEventDestroy(s.used);
+    s.built = s.used = nullptr;
 }
 
 template <typename P> P *alloc_n(Ctx &c, Structure &s, size_t n)
@@ -298,6 +329,49 @@ void run_build(Ctx &c, Structure &s)
         launch_kd(c, s);
     }
     s.tf_version = t.version;
+}
+
+// Restores the context stream when a build on the build stream ends or throws.
+struct OnStream {
+    Ctx &c;
+    cudaStream_t saved;
+    OnStream(Ctx &ctx, cudaStream_t s) : c(ctx), saved(ctx.stream) { c.stream = s; }
+    ~OnStream() { c.stream = saved; }
+};
+
+// run_build on the build stream, recording `built`; the structure's users
+// join it.  A first build starts after everything enqueued on the context
+// stream so far (its buffers were just allocated there); a rebuild only after
+// the last render of the structure and the last updates of its TF and volume,
+// so it can run while the context stream renders other structures.  The build
+// stream has the highest priority: the blocks of a rebuild are scheduled ahead
+// of those of a render running meanwhile.
+void run_build_async(Ctx &c, Structure &s, bool first)
+{
+    if (!c.build_stream) {
+        int least = 0, greatest = 0;
+        ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        ESS_CUDA(cudaStreamCreateWithPriority(&c.build_stream, cudaStreamNonBlocking, greatest));
+        ESS_CUDA(cudaEventCreateWithFlags(&c.fork_event, cudaEventDisableTiming));
+    }
+    if (!s.built) ESS_CUDA(cudaEventCreateWithFlags(&s.built, cudaEventDisableTiming));
+    if (first) {
+        ESS_CUDA(cudaEventRecord(c.fork_event, c.stream));
+        ESS_CUDA(cudaStreamWaitEvent(c.build_stream, c.fork_event, 0));
+    } else {
+        const cudaEvent_t deps[3] = {s.used, get_tf(c, s.tf).updated, get_vol(c, s.vol).updated};
+        for (cudaEvent_t e : deps)
+            if (e) ESS_CUDA(cudaStreamWaitEvent(c.build_stream, e, 0));
+    }
+    s.build_pending = true;
+    try {
+        OnStream on(c, c.build_stream);
+        run_build(c, s);
+    } catch (...) {
+        cudaEventRecord(s.built, c.build_stream);
+        throw;
+    }
+    ESS_CUDA(cudaEventRecord(s.built, c.build_stream));
 }
 
 int64_t nonempty_count(Ctx &c, Structure &s)
@@ -386,7 +460,10 @@ ess_status ess_destroy(ess_ctx *ctx)
                 if (kv.second->staging[k]) cudaFreeHost(kv.second->staging[k]);
                 if (kv.second->staged[k]) cudaEventDestroy(kv.second->staged[k]);
             }
+            if (kv.second->updated) cudaEventDestroy(kv.second->updated);
         }
+        for (auto &kv : c.volumes)
+            if (kv.second->updated) cudaEventDestroy(kv.second->updated);
         for (auto &p : c.pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -403,6 +480,8 @@ ess_status ess_destroy(ess_ctx *ctx)
             if (g.dev) cudaFree(g.dev);
         }
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
+        if (c.build_stream) cudaStreamDestroy(c.build_stream);
+        if (c.fork_event) cudaEventDestroy(c.fork_event);
         cudaFree(c.dev_status);
         cudaFree(c.samples);
         cudaFreeHost(c.host_status);
@@ -443,6 +522,7 @@ ess_status ess_release(ess_ctx *ctx, ess_handle h)
             c.free(v.data);
             c.free(v.cells);
             for (auto &m : v.minmax) c.free(m.second);
+            if (v.updated) cudaEventDestroy(v.updated);
             c.volumes.erase(h);
         } else if (tag == TAG_TF) {
             TF &t = get_tf(c, h);
@@ -454,6 +534,7 @@ ess_status ess_release(ess_ctx *ctx, ess_handle h)
                 if (t.staging[k]) cudaFreeHost(t.staging[k]);
                 if (t.staged[k]) cudaEventDestroy(t.staged[k]);
             }
+            if (t.updated) cudaEventDestroy(t.updated);
             c.tfs.erase(h);
         } else {
             throw Error{ESS_ERR_HANDLE, "unknown handle"};
@@ -513,7 +594,10 @@ ess_status ess_volume_set_sampler(ess_ctx *ctx, ess_handle vol, int cells)
 {
     return guard(ctx, [&](Ctx &c) {
         ESS_REQUIRE(cells == 0 || cells == 1, "sampler must be 0 (dense) or 1 (cells)");
-        set_sampler(c, get_vol(c, vol), cells);
+        join_all_builds(c);
+        Volume &v = get_vol(c, vol);
+        set_sampler(c, v, cells);
+        mark(c, v.updated);
     });
 }
 
@@ -545,6 +629,7 @@ ess_status ess_tf_update(ess_ctx *ctx, ess_handle tf, const float *rgba, int on_
         TF &t = get_tf(c, tf);
         ESS_REQUIRE(rgba, "null pointer");
         ESS_REQUIRE(nt == t.nt, "TF update must keep the table size");
+        join_all_builds(c);  // builds enqueued so far read the old table
         load_tf(c, t, rgba, on_device);
     });
 }
@@ -600,7 +685,7 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         }
         s->p = p;
         try {
-            if (kind != ESS_NONE) run_build(c, *s);
+            if (kind != ESS_NONE) run_build_async(c, *s, true);
             else s->tf_version = t.version;
         } catch (...) {
             free_structure(c, *s);
@@ -622,7 +707,7 @@ ess_status ess_rebuild(ess_ctx *ctx, ess_handle structure)
             s.tf_version = get_tf(c, s.tf).version;
             return;
         }
-        run_build(c, s);
+        run_build_async(c, s, false);
     });
 }
 
@@ -631,6 +716,7 @@ ess_status ess_structure_info_get(ess_ctx *ctx, ess_handle structure, ess_struct
     return guard(ctx, [&](Ctx &c) {
         ESS_REQUIRE(info, "null pointer");
         Structure &s = get_st(c, structure);
+        join_build(c, s);
         std::memset(info, 0, sizeof(*info));
         info->kind = s.kind;
         info->brick = s.p.brick;
@@ -663,6 +749,7 @@ ess_status ess_structure_read(ess_ctx *ctx, ess_handle structure, ess_array whic
         ESS_REQUIRE(dst || capacity == 0, "null destination");
         Structure &s = get_st(c, structure);
         ESS_REQUIRE(s.kind != ESS_NONE, "an ESS_NONE structure holds no arrays");
+        join_build(c, s);
         int64_t n = nonempty_count(c, s);
         switch (which) {
         case ESS_ARR_MINMAX: {
@@ -710,6 +797,7 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
         ESS_REQUIRE(camera && params && out, "null pointer");
         check_render_args(camera, params, W, H);
         Structure &s = get_st(c, structure);
+        join_build(c, s);
         Volume &v = get_vol(c, s.vol);
         TF &t = get_tf(c, s.tf);
         if (s.tf_version != t.version)
@@ -727,6 +815,7 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
         if (out_on_device) {
             j.out = out;
             launch_render(c, j);
+            mark(c, s.used);
         } else {
             if (c.stage_bytes < bytes) {
                 c.free(c.stage);
@@ -772,6 +861,7 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
             j.tile_w = tw;
             groups[((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)].push_back(j);
         }
+        for (int i = 0; i < count; ++i) join_build(c, get_st(c, items[i].structure));
         if (!c.capture_stream)
             ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
         for (auto &kv : groups) {
@@ -833,6 +923,13 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
             ESS_CUDA(cudaEventRecord(g.done[k], c.stream));
             g.next = (k + 1) % STAGE_RING;
         }
+        // later rebuilds of these structures wait for this batch
+        std::vector<Structure *> used;
+        for (int i = 0; i < count; ++i) {
+            Structure *p = &get_st(c, items[i].structure);
+            if (std::find(used.begin(), used.end(), p) == used.end()) used.push_back(p);
+        }
+        for (Structure *p : used) mark(c, p->used);
     });
 }
 
@@ -866,6 +963,7 @@ ess_status ess_autotune(ess_ctx *ctx, ess_handle vol, ess_handle tf, const ess_c
                     continue;  // e.g. LBVH beyond 1024 bricks per axis
                 }
                 Structure &s = get_st(c, h);
+                join_build(c, s);
                 // time one rebuild
                 ESS_CUDA(cudaEventRecord(e0, c.stream));
                 run_build(c, s);
@@ -940,6 +1038,7 @@ ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names, uint64_t 
 {
     return guard(ctx, [&](Ctx &c) {
         ESS_REQUIRE(count, "null pointer");
+        join_all_builds(c);
         ESS_CUDA(cudaStreamSynchronize(c.stream));
         for (auto &p : c.pending) {
             float ms = 0.0f;
@@ -970,6 +1069,7 @@ ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names, uint64_t 
 ess_status ess_profile_reset(ess_ctx *ctx)
 {
     return guard(ctx, [&](Ctx &c) {
+        join_all_builds(c);
         ESS_CUDA(cudaStreamSynchronize(c.stream));
         for (auto &p : c.pending) {
             c.free_events.push_back(p.a);

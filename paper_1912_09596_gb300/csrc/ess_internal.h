@@ -72,6 +72,7 @@ struct Volume {
     std::map<int, float2 *> minmax;  // per brick size: apron min/max (cached)
     int refs = 0;           // structures using the volume
     bool released = false;
+    cudaEvent_t updated = nullptr;  // after the last change of the cell copy
 };
 
 // Pinned staging slots per TF and per batch group: the host fills the next
@@ -90,6 +91,7 @@ struct TF {
     int stage_next = 0;
     int refs = 0;
     bool released = false;
+    cudaEvent_t updated = nullptr;  // after the last table upload and prefix
 };
 
 struct Structure {
@@ -140,6 +142,14 @@ struct Structure {
     cudaGraphExec_t kd_exec = nullptr;
     size_t device_bytes = 0;
     bool released = false;
+    // Builds run on the context's build stream: `built` is recorded after the
+    // last one, and users of the structure on the context stream wait for it
+    // first (join_build) while `build_pending` is set.  `used` is recorded on
+    // the context stream after each use of its buffers there (a render); a
+    // rebuild waits only for that, and for its TF and volume updates.
+    cudaEvent_t built = nullptr;
+    bool build_pending = false;
+    cudaEvent_t used = nullptr;
 };
 
 // The k-d renderer keeps a stack of 128 entries, enough for 129 levels.
@@ -181,6 +191,11 @@ struct Ctx {
     };
     std::map<int, BatchGroup> batch;
     cudaStream_t capture_stream = nullptr;
+    // Builds and rebuilds run here (highest priority), forked from and joined
+    // back into `stream` by events, so that a rebuild overlaps the rendering of
+    // other structures.
+    cudaStream_t build_stream = nullptr;
+    cudaEvent_t fork_event = nullptr;
 
     void *alloc(size_t bytes);
     void free(void *p);
@@ -190,6 +205,13 @@ struct Ctx {
     const char *current = nullptr;
     cudaEvent_t cur_a = nullptr;
 };
+
+// Builds run on Ctx::build_stream (ctx.cpp): the context stream waits for a
+// structure's last build, or for every build enqueued so far.
+void join_build(Ctx &c, Structure &s);
+void join_all_builds(Ctx &c);
+// Records `e` (created on first use, no timing) on the context stream.
+void mark(Ctx &c, cudaEvent_t &e);
 
 // Launch bracket: counts the launch, records profiling events and checks the
 // launch error.

@@ -372,6 +372,10 @@ ess_status ess_server_destroy(ess_server *s)
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     cudaStreamSynchronize(s->copy_stream);
+    try {
+        ess::join_all_builds(s->ctx->c);  // rebuilds of edits whose render failed
+    } catch (...) {
+    }
     cudaStreamSynchronize(s->ctx->c.stream);
     for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
     cudaStreamDestroy(s->copy_stream);
