@@ -152,22 +152,24 @@ def fp32_peak_tflops():
 
 # source files that define each kernel (by profiling-name prefix); every
 # kernel also depends on the shared internal header
-KERNEL_FILES = (("render", "render.cu"), ("brick_", "classify.cu"), ("compact", "classify.cu"),
-                ("tf_prefix", "classify.cu"), ("mask_cells", "classify.cu"),
-                ("build_cells", "classify.cu"), ("check_finite", "classify.cu"),
-                ("sort", "lbvh.cu"), ("lbvh", "lbvh.cu"), ("kd", "kd.cu"))
+KERNEL_FILES = (("render_shaded", ("render_shaded.cu", "render_kernels.h")),
+                ("render", ("render.cu", "render_kernels.h")), ("brick_", ("classify.cu",)),
+                ("compact", ("classify.cu",)), ("tf_prefix", ("classify.cu",)),
+                ("mask_cells", ("classify.cu",)), ("build_cells", ("classify.cu",)),
+                ("check_finite", ("classify.cu",)), ("sort", ("lbvh.cu",)),
+                ("lbvh", ("lbvh.cu",)), ("kd", ("kd.cu",)))
 
 
 def kernel_source_sha(kernel):
     """Hash of the source files that define `kernel` (None if unknown)."""
-    for prefix, fname in KERNEL_FILES:
+    for prefix, fnames in KERNEL_FILES:
         if kernel.startswith(prefix):
             break
     else:
         return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1912_09596_gb300", "csrc")
-    for f in (fname, "ess_internal.h"):
+    for f in fnames + ("ess_internal.h",):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -569,6 +571,49 @@ def run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, steps=3):
             "workload": "the main workload's 8 TF edits, one rebuild and one frame each", **res}
 
 
+SHADE = (0.25, 0.6, 0.3, 12)   # ka, kd, ks, shininess of the shaded workload
+
+
+def run_shaded(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, W, H, B, kd_params, steps=2):
+    """The second render workload: gradient shading (central differences of the
+    reconstruction, headlight Blinn-Phong) and opacity correction (dt 0.5 for
+    a TF defined per voxel) on the main workload's TF edits, one frame per
+    structure and edit, against the same frames unshaded (CUDA-event time per
+    frame; samples per frame are the same)."""
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    kinds = (ess.GRID, ess.LBVH, ess.KD)
+    sts = {k: ess.ess_build(ctx, vol, tf, k, ess.build_params(
+        brick=B, **(kd_params if k == ess.KD else {}))) for k in kinds}
+    rps = {"plain": ess.render_params(0.5, 0.99),
+           "shaded": ess.render_params(0.5, 0.99, shade=SHADE, dt_ref=1.0)}
+    res = {}
+    for name, rp in rps.items():
+        for rep in range(2):           # warm-up pass, then the timed one
+            ess.ess_sync(ctx)
+            ess.ess_profile_reset(ctx)
+            ess.ess_profile_enable(ctx, rep == 1)
+            for _ in range(steps if rep else 1):
+                for i in range(len(tf_dev)):
+                    ess.ess_tf_update(ctx, tf, tf_dev[i])
+                    for k in kinds:
+                        ess.ess_rebuild(ctx, sts[k])
+                    for k in kinds:
+                        ess.ess_render(ctx, sts[k], ecams[i], rp, W, H, out)
+            ess.ess_sync(ctx)
+        ess.ess_profile_enable(ctx, False)
+        prof = ess.ess_profile_read(ctx)
+        res[name] = {ess.KIND_NAMES[k]: round(
+            prof[("render_shaded_" if name == "shaded" else "render_") + ess.KIND_NAMES[k]][1] /
+            prof[("render_shaded_" if name == "shaded" else "render_") + ess.KIND_NAMES[k]][0], 4)
+            for k in kinds}
+    for st in sts.values():
+        ess.ess_release(ctx, st)
+    return {"workload": "the main workload's 8 TF edits, one 1024^2 frame per structure and edit; "
+                        "shading ka, kd, ks, shininess = %s, dt_ref 1 voxel" % (SHADE,),
+            "ms_per_frame": res,
+            "slowdown": {k: round(res["shaded"][k] / res["plain"][k], 3) for k in res["plain"]}}
+
+
 def run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, reps=3):
     """Table 1 / Table 2 style comparison on the main workload (Sec. 4.3): node
     count, height, build time and frame time of the LBVH and of the k-d tree
@@ -878,6 +923,10 @@ def run_ours(args, rank, local, ws, dist):
     if not args.no_hybrid:
         with torch.cuda.stream(stream):
             result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
+    if not args.no_shaded:
+        with torch.cuda.stream(stream):
+            result["shaded"] = run_shaded(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, W, H, B,
+                                          KD_PARAMS)
     if not args.no_structures:
         with torch.cuda.stream(stream):
             result["structures"] = run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams,
@@ -920,6 +969,8 @@ def main():
                     help="skip the brick min/max sweep over dtypes and sizes")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the hybrid-grid leg")
+    ap.add_argument("--no-shaded", action="store_true",
+                    help="skip the shaded-render workload (gradient shading, opacity correction)")
     ap.add_argument("--no-structures", action="store_true",
                     help="skip the structure comparison (node counts, heights, build and frame times)")
     args = ap.parse_args()

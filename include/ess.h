@@ -224,6 +224,20 @@ typedef struct {
     int tile_w;   /* warp tile width in pixels: 4, 8, 16 or 32 (0 = 8); the
                      warp covers tile_w x (32 / tile_w) pixels.  Does not
                      change the image. */
+    /* Second render workload (the paper switches both off, Sec. 4.1).
+     * Gradient shading: the gradient is the central difference of the
+     * trilinear reconstruction one voxel apart on each axis; samples of
+     * non-zero opacity get two-sided Blinn-Phong under a headlight,
+     * rgb' = rgb (ka + kd c) + ks c^shininess with c = min(|n . d|, 1),
+     * n = g / |g| (a zero gradient leaves rgb).  Zero-initialised fields give
+     * the unshaded renderer. */
+    int shading;       /* 0 off, 1 on */
+    float ka, kd, ks;  /* finite, >= 0 (used when shading is on) */
+    int shininess;     /* 1..128 (used when shading is on) */
+    /* Opacity correction: the TF's alpha holds for a step of dt_ref voxels;
+     * a sample taken every dt voxels gets 1 - (1 - alpha)^(dt / dt_ref).
+     * 0 switches it off; otherwise finite, > 0. */
+    float dt_ref;
 } ess_render_params;
 
 /* Ray-marches `structure` (Sec. 4.1: absorption plus emission,

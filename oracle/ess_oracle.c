@@ -16,6 +16,9 @@
  *   R7  early ray termination   S   sample lattice t_k = t_near + k*dt
  *   R8  LBVH child order        R9  k-d cost, halting, binning, max leaf size
  *   R10 Morton bit order        R11 IEEE float32, explicit fma
+ *   R13 gradient shading        R14 opacity correction
+ * (R13 and R14 are the second render workload: the paper only mentions
+ * gradient shading, which it switches off for its measurements, Sec. 4.1.)
  * Arithmetic: IEEE binary32 with every fused multiply-add written as fmaf()
  * and everything else single-rounded; build with -ffp-contract=off and
  * without fast-math.  The paper fixes no precision; the image oracle is float32
@@ -24,6 +27,11 @@
  * Parity status per function (pins live in tests/test_oracle_*.py):
  *   naive marcher: closed form (constant slab), special cases (all-empty,
  *     voxel centres, constant volume, exact table entries);
+ *   own log2/exp2: against float64 log2/exp2 over dense sweeps;
+ *   opacity correction: special cases (0, 1, ratio 1), closed form of a
+ *     constant slab and its independence of the step;
+ *   gradient and shading: exact gradients of linear ramps, closed-form shading
+ *     of ramp slabs, skipping invariance with both switched on;
  *   brick mask: brute-force point sampling on tiny volumes;
  *   Morton/sort: test vectors, library sort;
  *   LBVH: two independent constructions agree, 2n-1 nodes, Table 1 height
@@ -62,6 +70,10 @@ typedef struct {
     float dt;      /* step in voxels */
     float ert;     /* stop once accumulated alpha >= ert; > 1 disables */
     float bg[4];   /* background RGBA */
+    int shade;     /* R13: 0 off, 1 gradient shading */
+    float ka, kd, ks;
+    int shininess; /* 1..128 */
+    float dt_ref;  /* R14: 0 off, else the TF's alpha holds for this step */
 } ora_render_params;
 
 /* ------------------------------------------------------------------ R2 --- */
@@ -130,6 +142,99 @@ void ora_classify(const ora_tf *T, float value_lo, float s, float v, float out[4
     }
 }
 
+/* ------------------------------------------------------------ R13, R14 --- */
+static float f_of_bits(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+static uint32_t bits_of_f(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+/* log2 of x in (0, 1] (normal), from the series ln m = 2 atanh(u) =
+ * 2 (u + u^3/3 + u^5/5 + ...), u = (m - 1)/(m + 1), after splitting x = m 2^e
+ * with m in [sqrt(1/2), sqrt(2)]; terms to u^11 (|u| <= 0.1716). */
+float ora_log2_own(float x)
+{
+    uint32_t b = bits_of_f(x);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = f_of_bits((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 0x1.6a09e6p+0f) {  /* sqrt(2) */
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float u = (m - 1.0f) / (m + 1.0f);
+    float u2 = u * u;
+    float q = fmaf(u2, 0x1.745d18p-3f, 0x1.c71c72p-3f);  /* 2/11, 2/9 */
+    q = fmaf(u2, q, 0x1.24924ap-2f);                      /* 2/7 */
+    q = fmaf(u2, q, 0x1.99999ap-2f);                      /* 2/5 */
+    q = fmaf(u2, q, 0x1.555556p-1f);                      /* 2/3 */
+    q = fmaf(u2, q, 2.0f);
+    float ln_m = u * q;
+    return fmaf(ln_m, 0x1.715476p+0f, (float)e);          /* log2(e) */
+}
+
+/* 2^y for y <= 0: y = n + f with n = floor(y), f in [0, 1); 2^f = e^(f ln 2)
+ * by its Taylor series to the 10th power (Horner); then times 2^n.  Below
+ * 2^-126 the result is 0. */
+float ora_exp2_own(float y)
+{
+    if (y < -126.0f) return 0.0f;
+    float n = floorf(y);
+    float f = y - n;
+    float t = f * 0x1.62e430p-1f;  /* ln 2 */
+    float p = 0x1.27e4fcp-22f;     /* 1/10! */
+    p = fmaf(p, t, 0x1.71de3ap-19f);
+    p = fmaf(p, t, 0x1.a01a02p-16f);
+    p = fmaf(p, t, 0x1.a01a02p-13f);
+    p = fmaf(p, t, 0x1.6c16c2p-10f);
+    p = fmaf(p, t, 0x1.111112p-7f);
+    p = fmaf(p, t, 0x1.555556p-5f);
+    p = fmaf(p, t, 0x1.555556p-3f);
+    p = fmaf(p, t, 0.5f);
+    p = fmaf(p, t, 1.0f);
+    p = fmaf(p, t, 1.0f);
+    return p * f_of_bits((uint32_t)((int)n + 127) << 23);
+}
+
+/* R14: opacity of a sample taken every dt voxels when the TF's alpha holds
+ * for dt_ref voxels: 1 - (1 - alpha)^r, r = dt / dt_ref.  r = 0 (no
+ * correction) and r = 1 leave alpha as it is; alpha = 0 stays 0 and alpha = 1
+ * stays 1 exactly. */
+float ora_opacity_correct(float alpha, float r)
+{
+    if (r == 0.0f || r == 1.0f) return alpha;
+    float om = 1.0f - alpha;
+    if (om == 0.0f) return 1.0f;
+    return 1.0f - ora_exp2_own(r * ora_log2_own(om));
+}
+
+/* R13: gradient of the R2 reconstruction by central differences one voxel
+ * apart on each axis. */
+void ora_gradient(const ora_volume *V, float px, float py, float pz, float g[3])
+{
+    g[0] = (ora_sample_value(V, px + 1.0f, py, pz) - ora_sample_value(V, px - 1.0f, py, pz)) * 0.5f;
+    g[1] = (ora_sample_value(V, px, py + 1.0f, pz) - ora_sample_value(V, px, py - 1.0f, pz)) * 0.5f;
+    g[2] = (ora_sample_value(V, px, py, pz + 1.0f) - ora_sample_value(V, px, py, pz - 1.0f)) * 0.5f;
+}
+
+/* R13: two-sided Blinn-Phong under a headlight (light and eye along -d, so the
+ * half vector is the light): c = min(|n . d|, 1) with n = g / |g|;
+ * rgb' = rgb (ka + kd c) + ks c^shininess (power by squaring).  A zero
+ * gradient leaves rgb as it is. */
+void ora_shade(const float g[3], const float d[3], float ka, float kd, float ks, int shininess,
+               float rgb[3])
+{
+    float len2 = fmaf(g[2], g[2], fmaf(g[1], g[1], g[0] * g[0]));
+    if (!(len2 > 0.0f)) return;
+    float len = sqrtf(len2);
+    float dotv = fmaf(g[2], d[2], fmaf(g[1], d[1], g[0] * d[0]));
+    float c = fabsf(dotv) / len;
+    if (c > 1.0f) c = 1.0f;
+    float spec = 1.0f, base = c;
+    for (int e = shininess; e > 0; e >>= 1) {
+        if (e & 1) spec = spec * base;
+        if (e > 1) base = base * base;
+    }
+    float lam = fmaf(kd, c, ka), hs = ks * spec;
+    for (int i = 0; i < 3; ++i) rgb[i] = fmaf(rgb[i], lam, hs);
+}
+
 /* ------------------------------------------------------------------ R1 --- */
 /* Pixel (x, y), y = 0 the top row.  sx = (2x+1)/W - 1, sy = 1 - (2y+1)/H.
  * Perspective: o = eye, d = normalize(w + sx u + sy v).
@@ -185,22 +290,35 @@ static void volume_interval(const ora_volume *V, const float o[3], const float d
 /* ------------------------------------------------------- R6, R7, S ------- */
 typedef struct { float C[3], A; } ora_acc;
 
-/* One sample k of the ray (S: t_k = fmaf(k, dt, t_near)); composites it
- * front-to-back (R6, no opacity correction) and returns 1 once A >= ert (R7). */
+/* One sample k of the ray (S: t_k = fmaf(k, dt, t_near)); classifies it,
+ * corrects its opacity (R14) and shades it (R13, only if its opacity is not 0)
+ * when asked, composites it front-to-back (R6) and returns 1 once A >= ert
+ * (R7).  `r` is dt / dt_ref, or 0. */
 static int composite_sample(const ora_volume *V, const ora_tf *T, float s,
-                            const float o[3], const float d[3], float t, float ert,
-                            ora_acc *acc)
+                            const float o[3], const float d[3], float t,
+                            const ora_render_params *P, float r, ora_acc *acc)
 {
     float p0 = fmaf(t, d[0], o[0]), p1 = fmaf(t, d[1], o[1]), p2 = fmaf(t, d[2], o[2]);
     float val = ora_sample_value(V, p0, p1, p2);
     float rgba[4];
     ora_classify(T, V->value_lo, s, val, rgba);
+    rgba[3] = ora_opacity_correct(rgba[3], r);
+    if (P->shade && rgba[3] > 0.0f) {
+        float g[3];
+        ora_gradient(V, p0, p1, p2, g);
+        ora_shade(g, d, P->ka, P->kd, P->ks, P->shininess, rgba);
+    }
     float tr = (1.0f - acc->A) * rgba[3];
     acc->C[0] = fmaf(tr, rgba[0], acc->C[0]);
     acc->C[1] = fmaf(tr, rgba[1], acc->C[1]);
     acc->C[2] = fmaf(tr, rgba[2], acc->C[2]);
     acc->A = acc->A + tr;
-    return acc->A >= ert;
+    return acc->A >= P->ert;
+}
+
+static float step_ratio(const ora_render_params *P)
+{
+    return P->dt_ref > 0.0f ? P->dt / P->dt_ref : 0.0f;
 }
 
 static void finish_pixel(const ora_acc *acc, const float bg[4], float *px)
@@ -220,7 +338,7 @@ int64_t ora_render_naive(const ora_volume *V, const ora_tf *T, const ora_camera 
                          const ora_render_params *P, int W, int H, float *out,
                          int y0, int y1)
 {
-    float s = ora_tf_scale(V, T->nt);
+    float s = ora_tf_scale(V, T->nt), r = step_ratio(P);
     int64_t nsamp = 0;
     for (int y = y0; y < y1; ++y) {
         for (int x = 0; x < W; ++x) {
@@ -233,7 +351,7 @@ int64_t ora_render_naive(const ora_volume *V, const ora_tf *T, const ora_camera 
                     float t = fmaf((float)k, P->dt, tn);
                     if (!(t < tf)) break;
                     ++nsamp;
-                    if (composite_sample(V, T, s, o, d, t, P->ert, &acc)) break;
+                    if (composite_sample(V, T, s, o, d, t, P, r, &acc)) break;
                 }
             }
             finish_pixel(&acc, P->bg, out + 4 * ((size_t)y * W + x));
@@ -248,7 +366,7 @@ int64_t ora_render_pixels(const ora_volume *V, const ora_tf *T, const ora_camera
                           const ora_render_params *P, int W, int H, const int32_t *xy, int n,
                           float *out)
 {
-    float s = ora_tf_scale(V, T->nt);
+    float s = ora_tf_scale(V, T->nt), r = step_ratio(P);
     int64_t nsamp = 0;
     for (int i = 0; i < n; ++i) {
         float o[3], d[3], tn, tf;
@@ -260,7 +378,7 @@ int64_t ora_render_pixels(const ora_volume *V, const ora_tf *T, const ora_camera
                 float t = fmaf((float)k, P->dt, tn);
                 if (!(t < tf)) break;
                 ++nsamp;
-                if (composite_sample(V, T, s, o, d, t, P->ert, &acc)) break;
+                if (composite_sample(V, T, s, o, d, t, P, r, &acc)) break;
             }
         }
         finish_pixel(&acc, P->bg, out + 4 * (size_t)i);
@@ -293,7 +411,7 @@ int64_t ora_render_boxes(const ora_volume *V, const ora_tf *T, const ora_camera 
                          const ora_render_params *P, int W, int H, const float *boxes,
                          int nbox, float *out, int y0, int y1)
 {
-    float s = ora_tf_scale(V, T->nt);
+    float s = ora_tf_scale(V, T->nt), r = step_ratio(P);
     ora_iv *iv = (ora_iv *)malloc(sizeof(ora_iv) * (size_t)(nbox > 0 ? nbox : 1));
     int64_t nsamp = 0;
     for (int y = y0; y < y1; ++y) {
@@ -322,7 +440,7 @@ int64_t ora_render_boxes(const ora_volume *V, const ora_tf *T, const ora_camera 
                         float t = fmaf((float)k, P->dt, tn);
                         if (!(t < tf)) { done = 1; break; }
                         ++nsamp;
-                        if (composite_sample(V, T, s, o, d, t, P->ert, &acc)) { done = 1; break; }
+                        if (composite_sample(V, T, s, o, d, t, P, r, &acc)) { done = 1; break; }
                     }
                     if (k1 + 1 > k_next) k_next = k1 + 1;
                 }

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()``
 and by the benchmark's CPU-baseline leg, never by the library product.  The C
 file states the passage of the paper each function follows and the readings
-(R1..R11, S) taken where the paper is silent.
+(R1..R14, S) taken where the paper is silent.
 
 The C code is compiled with ``-ffp-contract=off`` and without fast-math so that
 its float32 arithmetic is exactly what the source says (every fused
@@ -56,7 +56,9 @@ class Camera(C.Structure):
 
 
 class RenderParams(C.Structure):
-    _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4)]
+    _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4),
+                ("shade", C.c_int), ("ka", C.c_float), ("kd", C.c_float), ("ks", C.c_float),
+                ("shininess", C.c_int), ("dt_ref", C.c_float)]
 
 
 def lib():
@@ -98,6 +100,14 @@ def lib():
             L.ora_lbvh_boxes.argtypes = [vp, i, i, i, vp, vp]
             L.ora_kd_build.argtypes = [vp, i, i, i, i, i, i, i, i, i, i, vp, i]
             L.ora_kd_build.restype = i
+            L.ora_log2_own.argtypes = [f]
+            L.ora_log2_own.restype = f
+            L.ora_exp2_own.argtypes = [f]
+            L.ora_exp2_own.restype = f
+            L.ora_opacity_correct.argtypes = [f, f]
+            L.ora_opacity_correct.restype = f
+            L.ora_gradient.argtypes = [P(Volume), f, f, f, vp]
+            L.ora_shade.argtypes = [vp, vp, f, f, f, i, vp]
             _lib = L
     return _lib
 
@@ -142,13 +152,46 @@ def camera_struct(cam) -> Camera:
     return c
 
 
-def params_struct(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0)) -> RenderParams:
+def params_struct(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), shade=None,
+                  dt_ref=0.0) -> RenderParams:
+    """`shade`: None (off) or (ka, kd, ks, shininess) for R13; `dt_ref` > 0
+    switches on the opacity correction of R14."""
     p = RenderParams()
     p.dt = dt
     p.ert = ert
     for i in range(4):
         p.bg[i] = float(bg[i])
+    if shade is not None:
+        p.shade = 1
+        p.ka, p.kd, p.ks = float(shade[0]), float(shade[1]), float(shade[2])
+        p.shininess = int(shade[3])
+    p.dt_ref = float(dt_ref)
     return p
+
+
+def log2_own(x):
+    return lib().ora_log2_own(float(x))
+
+
+def exp2_own(y):
+    return lib().ora_exp2_own(float(y))
+
+
+def opacity_correct(alpha, r):
+    return lib().ora_opacity_correct(float(alpha), float(r))
+
+
+def gradient(vol: "OVolume", p):
+    g = np.zeros(3, dtype=np.float32)
+    lib().ora_gradient(C.byref(vol.c), float(p[0]), float(p[1]), float(p[2]), _p(g))
+    return g
+
+
+def shade(g, d, ka, kd, ks, shininess, rgb):
+    g, d = (np.ascontiguousarray(a, dtype=np.float32) for a in (g, d))
+    out = np.array(rgb, dtype=np.float32)
+    lib().ora_shade(_p(g), _p(d), ka, kd, ks, int(shininess), _p(out))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -186,13 +229,13 @@ def _row_split(H, threads):
 
 
 def render_naive(vol: OVolume, tf: OTF, cam, W, H, dt=0.5, ert=2.0,
-                 bg=(0.0, 0.0, 0.0, 0.0), rows=None, threads=1):
+                 bg=(0.0, 0.0, 0.0, 0.0), rows=None, threads=1, shade=None, dt_ref=0.0):
     """Naive ray marching of rows [y0, y1) (default: all rows).  Returns
     (image (H, W, 4) float32 with only the requested rows filled, samples).
     `threads` > 1 renders row bands on parallel threads (ctypes drops the GIL)."""
     out = np.zeros((H, W, 4), dtype=np.float32)
     y0, y1 = (0, H) if rows is None else rows
-    cs, ps = camera_struct(cam), params_struct(dt, ert, bg)
+    cs, ps = camera_struct(cam), params_struct(dt, ert, bg, shade, dt_ref)
     L = lib()
     counts = []
 
@@ -213,12 +256,12 @@ def render_naive(vol: OVolume, tf: OTF, cam, W, H, dt=0.5, ert=2.0,
 
 
 def render_pixels(vol: OVolume, tf: OTF, cam, W, H, xy, dt=0.5, ert=2.0,
-                  bg=(0.0, 0.0, 0.0, 0.0), threads=1):
+                  bg=(0.0, 0.0, 0.0, 0.0), threads=1, shade=None, dt_ref=0.0):
     """Naive marching of the pixels `xy` ((n, 2) int: x, y).  Returns the
     (n, 4) pixels and the number of samples taken."""
     xy = np.ascontiguousarray(np.asarray(xy, dtype=np.int32).reshape(-1, 2))
     out = np.zeros((xy.shape[0], 4), dtype=np.float32)
-    cs, ps = camera_struct(cam), params_struct(dt, ert, bg)
+    cs, ps = camera_struct(cam), params_struct(dt, ert, bg, shade, dt_ref)
     L = lib()
     counts = []
 
@@ -237,13 +280,13 @@ def render_pixels(vol: OVolume, tf: OTF, cam, W, H, xy, dt=0.5, ert=2.0,
 
 
 def render_boxes(vol: OVolume, tf: OTF, cam, W, H, boxes, dt=0.5, ert=2.0,
-                 bg=(0.0, 0.0, 0.0, 0.0), rows=None):
+                 bg=(0.0, 0.0, 0.0, 0.0), rows=None, shade=None, dt_ref=0.0):
     """Skipping render by brute-force interval enumeration (rule S) over the
     closed voxel-space boxes `boxes` (m, 6) = lo xyz, hi xyz."""
     out = np.zeros((H, W, 4), dtype=np.float32)
     y0, y1 = (0, H) if rows is None else rows
     b = np.ascontiguousarray(np.asarray(boxes, dtype=np.float32).reshape(-1, 6))
-    cs, ps = camera_struct(cam), params_struct(dt, ert, bg)
+    cs, ps = camera_struct(cam), params_struct(dt, ert, bg, shade, dt_ref)
     n = lib().ora_render_boxes(C.byref(vol.c), C.byref(tf.c), C.byref(cs), C.byref(ps),
                                W, H, _p(b), b.shape[0], _p(out), y0, y1)
     return out, int(n)

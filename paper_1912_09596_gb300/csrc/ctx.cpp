@@ -399,6 +399,17 @@ void check_render_args(const ess_camera *camera, const ess_render_params *params
                     "camera must be finite");
     ESS_REQUIRE(camera->w[0] != 0.0f || camera->w[1] != 0.0f || camera->w[2] != 0.0f,
                 "camera needs a non-zero forward vector");
+    ESS_REQUIRE(params->shading == 0 || params->shading == 1, "shading must be 0 or 1");
+    if (params->shading) {
+        ESS_REQUIRE(std::isfinite(params->ka) && std::isfinite(params->kd) &&
+                        std::isfinite(params->ks) && params->ka >= 0.0f && params->kd >= 0.0f &&
+                        params->ks >= 0.0f,
+                    "ka, kd, ks must be finite and >= 0");
+        ESS_REQUIRE(params->shininess >= 1 && params->shininess <= 128,
+                    "shininess must be in 1..128");
+    }
+    ESS_REQUIRE(std::isfinite(params->dt_ref) && params->dt_ref >= 0.0f,
+                "dt_ref must be 0 (no opacity correction) or finite and > 0");
 }
 
 void copy_out(Ctx &c, void *dst, const void *src, size_t bytes, size_t cap, size_t *written)
@@ -859,7 +870,9 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
             j.H = it.H;
             j.out = it.out;
             j.tile_w = tw;
-            groups[((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)].push_back(j);
+            const int shaded = render_shaded(it.params) ? 1 : 0;
+            groups[(((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)) * 2 + shaded]
+                .push_back(j);
         }
         for (int i = 0; i < count; ++i) join_build(c, get_st(c, items[i].structure));
         if (!c.capture_stream)
@@ -890,7 +903,8 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
                 try {
                     if (e1 == cudaSuccess)
                         launch_render_batch(c, jobs[0].st->kind, jobs[0].vol->dtype,
-                                            jobs[0].vol->use_cells, g.dev);
+                                            jobs[0].vol->use_cells, render_shaded(jobs[0].rp),
+                                            g.dev);
                 } catch (...) {
                     c.stream = saved;
                     cudaGraph_t tmp;

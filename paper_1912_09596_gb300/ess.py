@@ -51,7 +51,8 @@ class Camera(C.Structure):
 
 class RenderParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("ert", C.c_float), ("bg", C.c_float * 4),
-                ("tile_w", C.c_int)]
+                ("tile_w", C.c_int), ("shading", C.c_int), ("ka", C.c_float), ("kd", C.c_float),
+                ("ks", C.c_float), ("shininess", C.c_int), ("dt_ref", C.c_float)]
 
 
 class RenderItem(C.Structure):
@@ -269,13 +270,20 @@ def camera_from(cam):
     return camera(cam.eye, cam.u, cam.v, cam.w, cam.ortho)
 
 
-def render_params(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), tile_w=0):
+def render_params(dt=0.5, ert=2.0, bg=(0.0, 0.0, 0.0, 0.0), tile_w=0, shade=None, dt_ref=0.0):
+    """`shade`: None (off) or (ka, kd, ks, shininess) for gradient shading;
+    `dt_ref` > 0 switches on the opacity correction."""
     p = RenderParams()
     p.dt = dt
     p.ert = ert
     for i in range(4):
         p.bg[i] = float(bg[i])
     p.tile_w = int(tile_w)
+    if shade is not None:
+        p.shading = 1
+        p.ka, p.kd, p.ks = float(shade[0]), float(shade[1]), float(shade[2])
+        p.shininess = int(shade[3])
+    p.dt_ref = float(dt_ref)
     return p
 
 

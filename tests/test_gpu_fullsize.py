@@ -93,3 +93,32 @@ def test_fractal1024_f32_mask_and_sampled_pixels(gpu, ctx, ora):
         ess.ess_sync(ctx)
         _check_pixels(out.cpu().numpy(), xy, ref, "fractal1024 %s" % ess.KIND_NAMES[kind])
         ess.ess_release(ctx, st)
+
+
+def test_ct512_shaded_sampled_pixels(gpu, ctx, ora, ct512):
+    """The second render workload at the benchmark's size: gradient shading
+    and opacity correction (dt 0.5 against dt_ref 1) on full 1024^2 frames of
+    the 512^3 workload, sampled pixels against the oracle."""
+    ess, torch = gpu
+    vol_np, tfs, cams = ct512
+    W = H = 1024
+    shade = (0.25, 0.6, 0.3, 12)
+    ov = ora.OVolume(vol_np, 0, 255)
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).cuda(), 0, 255)
+    rp = ess.render_params(0.5, 0.99, shade=shade, dt_ref=1.0)
+    for ti in (2, 6):
+        ot = ora.OTF(tfs[ti])
+        t = ess.ess_tf_set(ctx, torch.from_numpy(tfs[ti]).cuda())
+        xy = _pixels(W, H, 128, seed=10 + ti)
+        ref, _ = ora.render_pixels(ov, ot, cams[ti], W, H, xy, dt=0.5, ert=0.99, threads=8,
+                                   shade=shade, dt_ref=1.0)
+        for kind, params in ((ess.GRID, {}), (ess.LBVH, {}),
+                             (ess.KD, dict(nbins=4, halting=1, mls=32))):
+            st = ess.ess_build(ctx, vol, t, kind, ess.build_params(brick=8, **params))
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+            ess.ess_render(ctx, st, cams[ti], rp, W, H, out)
+            ess.ess_sync(ctx)
+            _check_pixels(out.cpu().numpy(), xy, ref,
+                          "ct512 shaded TF %d %s" % (ti, ess.KIND_NAMES[kind]))
+            ess.ess_release(ctx, st)
+        ess.ess_release(ctx, t)
