@@ -321,7 +321,8 @@ __device__ __forceinline__ float own_exp2(float y)
 // for dt_ref (r = dt / dt_ref); r = 0 or 1 leaves alpha, 0 and 1 stay fixed.
 __device__ __forceinline__ float correct_alpha(float alpha, float r)
 {
-    if (r == 0.0f || r == 1.0f) return alpha;
+    // alpha 0 gives 1 - 2^(r log2 1) = 1 - 2^0 = 0 exactly: skip the series
+    if (r == 0.0f || r == 1.0f || alpha == 0.0f) return alpha;
     const float om = 1.0f - alpha;
     if (om == 0.0f) return 1.0f;
     return 1.0f - own_exp2(r * own_log2(om));
