@@ -390,6 +390,19 @@ ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names,
                             uint64_t *launches, double *total_ms, int *count);
 ess_status ess_profile_reset(ess_ctx *ctx);
 
+/* ----------------------------------------------------------- diagnostics */
+
+/* Failure-detection check of the device-side waits.  Every wait of the
+ * library's kernels on another block (the radix sort's look-back) is bounded:
+ * after a fixed number of polls the kernel records a timeout in the context's
+ * status word, stops waiting and returns, and the next ess_sync reports
+ * ESS_ERR_TIMEOUT while the context stays usable.  This call runs that same
+ * bounded wait in one warp on a device flag: with `set` = 1 the flag is set
+ * first and the wait ends at once; with `set` = 0 nothing sets it and the wait
+ * gives up after `polls` polls (1 <= polls <= 2^24).  Asynchronous on the
+ * context stream. */
+ess_status ess_selftest_wait(ess_ctx *ctx, int set, int64_t polls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -465,6 +465,7 @@ ess_status ess_destroy(ess_ctx *ctx)
             c.free(kv.second->prefix);
         }
         c.free(c.stage);
+        c.free(c.selftest_flag);
         ESS_CUDA(cudaStreamSynchronize(c.stream));
         for (auto &kv : c.tfs) {
             for (int k = 0; k < STAGE_RING; ++k) {
@@ -1077,6 +1078,16 @@ ess_status ess_profile_read(ess_ctx *ctx, int max, const char **names, uint64_t 
             ++k;
         }
         *count = k;
+    });
+}
+
+ess_status ess_selftest_wait(ess_ctx *ctx, int set, int64_t polls)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(set == 0 || set == 1, "set must be 0 or 1");
+        ESS_REQUIRE(polls >= 1 && polls <= (int64_t)1 << 24, "polls must be in 1..2^24");
+        if (!c.selftest_flag) c.selftest_flag = (uint32_t *)c.alloc(sizeof(uint32_t));
+        launch_selftest_wait(c, c.selftest_flag, set == 1, (long)polls);
     });
 }
 

@@ -196,6 +196,7 @@ struct Ctx {
     // other structures.
     cudaStream_t build_stream = nullptr;
     cudaEvent_t fork_event = nullptr;
+    uint32_t *selftest_flag = nullptr;  // device word of ess_selftest_wait
 
     void *alloc(size_t bytes);
     void free(void *p);
@@ -243,6 +244,7 @@ int launch_radix_sort(Ctx &c, const uint32_t *keys, const uint32_t *vals, uint32
                       int64_t cap, int bits, uint32_t *scratch);
 void launch_lbvh(Ctx &c, Structure &s);
 int lbvh_height(Ctx &c, Structure &s);
+void launch_selftest_wait(Ctx &c, uint32_t *flag, bool set, long limit);
 
 // kd.cu
 void launch_kd(Ctx &c, Structure &s);

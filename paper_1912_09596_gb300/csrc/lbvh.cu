@@ -33,6 +33,23 @@ constexpr int RS_RADIX = 256;
 constexpr uint32_t RS_FLAG_AGG = 1u << 30, RS_FLAG_INC = 2u << 30, RS_MASK = (1u << 30) - 1;
 constexpr long RS_SPIN_LIMIT = 1L << 22;
 
+// The bounded wait of the look-back: polls *p until one of the bits of `mask`
+// is set or `limit` polls have passed; on a timeout records DEV_ERR_TIMEOUT.
+// Returns the last value read (none of the `mask` bits set after a timeout).
+__device__ __forceinline__ uint32_t poll_flag(const volatile uint32_t *p, uint32_t mask, long limit,
+                                              uint32_t *status)
+{
+    uint32_t v;
+    long spins = 0;
+    while (((v = *p) & mask) == 0u) {
+        if (++spins > limit) {
+            atomicOr(status, DEV_ERR_TIMEOUT);
+            break;
+        }
+    }
+    return v;
+}
+
 size_t sort_tiles(int64_t cap) { return (size_t)((cap + RS_TILE - 1) / RS_TILE); }
 
 size_t sort_scratch_words(int64_t cap)
@@ -150,17 +167,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_pass(
         } else {
             st[(size_t)tile * RS_RADIX + t] = RS_FLAG_AGG | cnt;
             int64_t j = (int64_t)tile - 1;
-            long spins = 0;
             while (j >= 0) {
-                uint32_t v = st[(size_t)j * RS_RADIX + t];
-                uint32_t f = v & ~RS_MASK;
-                if (f == 0u) {
-                    if (++spins > RS_SPIN_LIMIT) {
-                        atomicOr(status, DEV_ERR_TIMEOUT);
-                        break;
-                    }
-                    continue;
-                }
+                const uint32_t v = poll_flag(st + (size_t)j * RS_RADIX + t, ~RS_MASK, RS_SPIN_LIMIT,
+                                             status);
+                const uint32_t f = v & ~RS_MASK;
+                if (f == 0u) break;  // timed out
                 excl += v & RS_MASK;
                 if (f == RS_FLAG_INC) break;
                 --j;
@@ -388,6 +399,19 @@ __global__ void k_lbvh_height(const int *__restrict__ count, const int32_t *__re
         }
     }
     atomicMax(height, h);
+}
+
+// Diagnostics: one warp waits on `flag` with the look-back's bounded wait.
+__global__ void k_selftest_wait(const uint32_t *flag, long limit, uint32_t *status)
+{
+    if (threadIdx.x == 0) poll_flag(flag, 1u, limit, status);
+}
+
+void launch_selftest_wait(Ctx &c, uint32_t *flag, bool set, long limit)
+{
+    ESS_CUDA(cudaMemsetAsync(flag, set ? 0xff : 0, sizeof(uint32_t), c.stream));
+    Launch L(c, "selftest_wait");
+    k_selftest_wait<<<1, 32, 0, c.stream>>>(flag, limit, c.dev_status);
 }
 
 void launch_lbvh(Ctx &c, Structure &s)

@@ -115,6 +115,7 @@ def _load():
         "ess_profile_enable": [vp, i],
         "ess_profile_read": [vp, i, P(C.c_char_p), P(C.c_uint64), P(C.c_double), P(i)],
         "ess_profile_reset": [vp],
+        "ess_selftest_wait": [vp, i, C.c_int64],
         "ess_compact_mask_noalloc": [vp, C.c_int64, vp, vp, vp],
         "ess_render_batch": [vp, P(RenderItem), i, i],
         "ess_server_create": [vp, P(ServerConfig), P(vp)],
@@ -412,3 +413,7 @@ def ess_profile_read(ctx):
 
 def ess_profile_reset(ctx):
     _check(ctx, lib.ess_profile_reset(ctx))
+
+
+def ess_selftest_wait(ctx, set_flag, polls):
+    _check(ctx, lib.ess_selftest_wait(ctx, int(bool(set_flag)), int(polls)))
