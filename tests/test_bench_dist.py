@@ -67,3 +67,42 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
 
     bench.run_reference(Args(), rank=1)           # other ranks exit without work
     assert capsys.readouterr().out == ""
+
+
+def _rank_fail_main(rank, world, port, out_dir):
+    """Rank 1 joins the group and then dies before the timing collective, as a
+    failed replica would; rank 0 must get an error from its collective within
+    the process group's timeout instead of waiting for ever."""
+    import datetime
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import bench
+    _, _, ws, dist = bench.dist_setup()
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    if rank == 1:
+        os._exit(3)
+    try:
+        bench.max_over_ranks(dist, 10.0, "cpu")
+        result = "no error"
+    except Exception as e:  # the collective fails: peer gone or timed out
+        result = "error " + type(e).__name__
+    with open(os.path.join(out_dir, "rank0.txt"), "w") as f:
+        f.write(result)
+    os._exit(0)
+
+
+@pytest.mark.timeout(120)
+def test_failed_replica_is_detected_not_waited_for(tmp_path):
+    pytest.importorskip("torch")
+    import multiprocessing
+    sp = multiprocessing.get_context("spawn")
+    port = _free_port()
+    procs = [sp.Process(target=_rank_fail_main, args=(r, 2, port, str(tmp_path))) for r in (0, 1)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=90)
+    assert [p.exitcode for p in procs] == [0, 3]
+    assert open(tmp_path / "rank0.txt").read().startswith("error")
