@@ -831,6 +831,19 @@ def run_ours(args, rank, local, ws, dist):
         ess.ess_sync(ctx)
         e2e_ms = max_over_ranks(dist, 1000.0 * (time.perf_counter() - t0), dev)
 
+        # the step's rebuilds alone (no frame beside them): per edit, the TF
+        # upload and the three rebuilds, waited for before the next edit
+        ess.ess_profile_reset(ctx)
+        ess.ess_profile_enable(ctx, True)
+        for _ in range(args.steps):
+            for i in range(len(tfs_np)):
+                ess.ess_tf_update(ctx, tf, tf_dev[i])
+                for k in kinds:
+                    ess.ess_rebuild(ctx, st[k])
+                ess.ess_sync(ctx)
+        ess.ess_profile_enable(ctx, False)
+        prof_alone = ess.ess_profile_read(ctx)
+
     units_step = sum(n_naive) * len(kinds)
     evaluated_step = sum(sum(v) for v in n_eval.values())
     value = job_rate(units_step, ws, args.steps, t_ms)
@@ -903,8 +916,9 @@ def run_ours(args, rank, local, ws, dist):
     edits = args.steps * len(tfs_np)
     build_ms["all_structures_per_edit"] = total_build_ms / edits
     build_ms["note"] = ("event intervals of the build kernels on the library's build stream, which "
-                        "run while the frames of the same edit render; the structures object "
-                        "times each build alone")
+                        "run while the frames of the same edit render")
+    build_ms["alone_per_edit"] = sum(v[1] for v in prof_alone.values()) / edits
+    build_ms["alone_by_kernel"] = {nm: round(v[1] / edits, 4) for nm, v in prof_alone.items()}
 
     result = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
