@@ -406,12 +406,13 @@ def serve_requests(ess, scene, n, seed):
     return reqs
 
 
-def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
+def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=3.0):
     """Poisson stream of render and TF-edit requests (30 % edits) over 6
     resident volumes, image sizes 256^2 .. 1920x1080.  Serial plain processing
     (one request at a time through ess_render with a host image) against the
     continuous-batching server, both fed at the same arrival times; the rate is
-    `load` times the serial service rate measured first."""
+    `load` times the serial service rate measured first, so that both arms are
+    busy and their throughputs are their capacities."""
     import threading
     scene = serve_scene(ess, torch, dev, ctx, ct512)
     reqs = serve_requests(ess, scene, n_req, seed=11)
@@ -435,14 +436,14 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
     # a lot in cost, so a short prefix would be a noisy estimate); median of
     # three passes after an untimed one
     rates = []
-    for _ in range(4):
+    for _ in range(5):
         reset()
         t0 = time.perf_counter()
         for r, o in zip(reqs, outs):
             serve_one(r, o)
         ess.ess_sync(ctx)
         rates.append(n_req / (time.perf_counter() - t0))
-    mu = float(np.median(rates[1:]))
+    mu = float(np.median(rates[2:]))
     lam = load * mu
     gaps = np.random.default_rng(12).exponential(1.0 / lam, size=n_req)
     arrivals = np.cumsum(gaps)
@@ -488,9 +489,17 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
 
     # plain and served alternate REPS times at the same arrival times; each
     # arm reports its repetition of median throughput (the host is shared, so
-    # a single repetition can catch a stall of either arm)
+    # a single repetition can catch a stall of either arm).  Clocks are
+    # sampled before and after the repetitions, not during them: an
+    # nvidia-smi query can hold up these host-driven request loops.
     REPS = 3
-    clocks = ClockSampler(torch.cuda.current_device())
+
+    def clock_snapshot():
+        sampler = ClockSampler(torch.cuda.current_device())
+        time.sleep(0.5)
+        return sampler.stop()
+
+    clk_before = clock_snapshot()
     plain_runs, served_runs = [], []
     same = True
     for rep in range(REPS):
@@ -503,7 +512,7 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
         served_runs.append((n_req / span_served, st, t_sub))
         # the served images must equal the serial ones: both apply the same edits in order
         same = same and all(torch.equal(a, b) for a, b in zip(plain_imgs, outs))
-    clk = clocks.stop()
+    clk = {"before": clk_before, "after": clock_snapshot()}
     pct = lambda a, q: float(np.percentile(np.asarray(a), q))
     med = lambda runs: sorted(runs, key=lambda x: x[0])[len(runs) // 2]
     fps_plain, lat_plain = med(plain_runs)
@@ -515,7 +524,8 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=1.5):
     ok = all(x["status"] == ess.OK for r in served_runs for x in r[1])
     return {
         "workload": "6 resident volumes (" + ", ".join(s["name"] for s in scene) + "), kinds "
-                    "grid/lbvh/kd in turn, brick 8; Poisson arrivals, 30% TF edits (rebuild), "
+                    "grid/lbvh/kd in turn, brick 8; Poisson arrivals at %.1fx the serial service "
+                    "rate, 30%% TF edits (rebuild), " % load +
                     "image sizes 256^2..1920x1080, dt 0.5, ERT 0.99; images read back to pinned "
                     "host memory",
         "requests": n_req, "rate_hz": round(lam, 2), "serial_service_rate_hz": round(mu, 2),
