@@ -704,9 +704,13 @@ def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
             ess.ess_profile_reset(ctx)
             ess.ess_profile_enable(ctx, True)
             for _ in range(reps):
+                # the rebuild runs on the library's build stream, which does not
+                # wait for this stream: finish the flush first, and the rebuild
+                # before the next flush
                 flush.zero_()
+                torch.cuda.synchronize(dev)
                 ess.ess_rebuild(ctx, st)
-            ess.ess_sync(ctx)
+                ess.ess_sync(ctx)
             ess.ess_profile_enable(ctx, False)
             n, ms = ess.ess_profile_read(ctx)["brick_minmax"]
             nb = 1
