@@ -244,8 +244,10 @@ typedef struct {
  * post-classification) into a W x H RGBA image.  Pixel (x, y) shoots the ray
  * through sx = (2x+1)/W - 1, sy = 1 - (2y+1)/H; samples sit at
  * t_k = t_near + k*dt on every path; skipping drops only samples of zero
- * opacity, so the image equals naive marching.  ESS_ERR_STALE if the TF was
- * updated after the build. */
+ * opacity, so the image equals naive marching, with or without gradient
+ * shading and opacity correction (both leave zero opacity at zero).
+ * ESS_ERR_STALE if the TF was updated after the build; ESS_ERR_ARG for
+ * parameters outside the ranges stated above. */
 ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *camera,
                       const ess_render_params *params, int W, int H, float *out,
                       int out_on_device);
