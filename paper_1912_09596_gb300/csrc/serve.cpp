@@ -19,6 +19,7 @@
 // see (the batch is cut there).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -290,6 +291,18 @@ ess_status ess_server_create(ess_ctx *ctx, const ess_server_config *cfg, ess_ser
         cudaStreamDestroy(s->copy_stream);
         delete s;
         return ESS_ERR_CUDA;
+    }
+    // Grow the pool once now (up to 1 GiB of the budget, kept by the release
+    // threshold), so that the first batches do not wait for it to map memory.
+    {
+        const size_t warm = std::min<size_t>(c.memory_budget, (size_t)1 << 30);
+        void *p = nullptr;
+        if (cudaMallocFromPoolAsync(&p, warm, s->pool, s->copy_stream) == cudaSuccess) {
+            cudaFreeAsync(p, s->copy_stream);
+        } else {
+            cudaGetLastError();
+        }
+        cudaStreamSynchronize(s->copy_stream);
     }
     s->worker = std::thread(worker_loop, s);
     *out = s;
