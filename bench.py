@@ -350,12 +350,56 @@ def run_batched(ess, torch, dev, stream, ctx, reps=3):
            "plain_frames_per_s": 256 / (t_plain / 1000.0),
            "batched_frames_per_s": 256 / (t_batch / 1000.0),
            "speedup": t_plain / t_batch, "bit_identical": bool(same)}
+    out["rebuild"] = run_rebuild_batch(ess, torch, dev, ctx, vol, tf_handles, sts, reps)
     for st in sts:
         ess.ess_release(ctx, st)
     for t in tf_handles:
         ess.ess_release(ctx, t)
     ess.ess_release(ctx, vol)
     return out
+
+
+def run_rebuild_batch(ess, torch, dev, ctx, vol, tf_handles, sts, reps):
+    """The batched build of the TF structures: one ess_rebuild per structure
+    against one ess_rebuild_batch of them all, host wall time from the first
+    call to the end of the last build (median of `reps`), for the render
+    batch's 64 autotuned structures and for 16 TFs x {grid, LBVH, k-d} built
+    with a min/max rescan (the benchmark step's parameters).  The batch's
+    masks must equal the one-by-one rebuilds' masks."""
+    def wall(fn):
+        fn()
+        ess.ess_sync(ctx)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            fn()
+            ess.ess_sync(ctx)
+            ts.append(1000.0 * (time.perf_counter() - t0))
+        return float(np.median(ts))
+
+    def compare(handles):
+        one = lambda: [ess.ess_rebuild(ctx, h) for h in handles]
+        batch = lambda: ess.ess_rebuild_batch(ctx, handles)
+        t_one, t_batch = wall(one), wall(batch)
+        masks = [ess.ess_structure_read(ctx, h, ess.ARR_MASK) for h in handles]
+        one()
+        same = all(np.array_equal(m, ess.ess_structure_read(ctx, h, ess.ARR_MASK))
+                   for m, h in zip(masks, handles))
+        return {"structures": len(handles), "one_by_one_ms": round(t_one, 3),
+                "batched_ms": round(t_batch, 3), "speedup": round(t_one / t_batch, 2),
+                "masks_identical": bool(same)}
+
+    res = {"autotuned_64": compare(sts)}
+    mixed = []
+    for t in tf_handles[:16]:
+        for k in (ess.GRID, ess.LBVH, ess.KD):
+            mixed.append(ess.ess_build(ctx, vol, t, k, ess.build_params(brick=8, rescan=1,
+                                                                        **KD_PARAMS)))
+    res["grid_lbvh_kd_48_rescan"] = compare(mixed)
+    for h in mixed:
+        ess.ess_release(ctx, h)
+    return res
 
 
 SERVE_SIZES = [(256, 256), (512, 512), (1024, 768), (1920, 1080)]

@@ -168,6 +168,16 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
  * reusing its device memory: the per-edit hot path of Sec. 1. */
 ess_status ess_rebuild(ess_ctx *ctx, ess_handle structure);
 
+/* Rebuilds `count` distinct structures (1 <= count <= 4096), e.g. one per TF
+ * of a batch of many TFs over one volume, with the same results as calling
+ * ess_rebuild on each.  Together: the per-brick min/max of structures built
+ * with rescan = 1 is recomputed once per (volume, brick size) of the batch,
+ * not once per structure, and the structures' build chains run on several
+ * internal streams at once, so that their latency-bound kernels overlap.
+ * Asynchronous; later users of each structure wait for its build as usual.
+ * ESS_ERR_ARG for a repeated handle, ESS_ERR_HANDLE for a bad one. */
+ess_status ess_rebuild_batch(ess_ctx *ctx, const ess_handle *structures, int count);
+
 typedef struct {
     int kind, brick;
     int gx, gy, gz;          /* brick grid = ceil(n / brick) per axis */

@@ -91,6 +91,10 @@ void join_all_builds(Ctx &c)
     if (!c.build_stream) return;
     ESS_CUDA(cudaEventRecord(c.fork_event, c.build_stream));
     ESS_CUDA(cudaStreamWaitEvent(c.stream, c.fork_event, 0));
+    for (cudaStream_t st : c.batch_streams) {
+        ESS_CUDA(cudaEventRecord(c.fork_event, st));
+        ESS_CUDA(cudaStreamWaitEvent(c.stream, c.fork_event, 0));
+    }
     for (auto &kv : c.structures) kv.second->build_pending = false;
 }
 
@@ -346,33 +350,55 @@ struct OnStream {
 // so it can run while the context stream renders other structures.  The build
 // stream has the highest priority: the blocks of a rebuild are scheduled ahead
 // of those of a render running meanwhile.
+void ensure_build_stream(Ctx &c)
+{
+    if (c.build_stream) return;
+    int least = 0, greatest = 0;
+    ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    ESS_CUDA(cudaStreamCreateWithPriority(&c.build_stream, cudaStreamNonBlocking, greatest));
+    ESS_CUDA(cudaEventCreateWithFlags(&c.fork_event, cudaEventDisableTiming));
+}
+
+// `st` waits for what a rebuild of `s` must follow: its last render, the last
+// updates of its TF and volume, and its previous build (on whichever stream).
+void wait_rebuild_deps(Ctx &c, Structure &s, cudaStream_t st)
+{
+    const cudaEvent_t deps[3] = {s.used, get_tf(c, s.tf).updated, get_vol(c, s.vol).updated};
+    for (cudaEvent_t e : deps)
+        if (e) ESS_CUDA(cudaStreamWaitEvent(st, e, 0));
+    if (s.build_pending) ESS_CUDA(cudaStreamWaitEvent(st, s.built, 0));
+}
+
+// run_build on stream `st`, recording `built`.
+void build_on(Ctx &c, Structure &s, cudaStream_t st)
+{
+    if (!s.built) ESS_CUDA(cudaEventCreateWithFlags(&s.built, cudaEventDisableTiming));
+    s.build_pending = true;
+    try {
+        OnStream on(c, st);
+        run_build(c, s);
+    } catch (...) {
+        cudaEventRecord(s.built, st);
+        throw;
+    }
+    ESS_CUDA(cudaEventRecord(s.built, st));
+}
+
 void run_build_async(Ctx &c, Structure &s, bool first)
 {
-    if (!c.build_stream) {
-        int least = 0, greatest = 0;
-        ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-        ESS_CUDA(cudaStreamCreateWithPriority(&c.build_stream, cudaStreamNonBlocking, greatest));
-        ESS_CUDA(cudaEventCreateWithFlags(&c.fork_event, cudaEventDisableTiming));
-    }
-    if (!s.built) ESS_CUDA(cudaEventCreateWithFlags(&s.built, cudaEventDisableTiming));
+    ensure_build_stream(c);
     if (first) {
         ESS_CUDA(cudaEventRecord(c.fork_event, c.stream));
         ESS_CUDA(cudaStreamWaitEvent(c.build_stream, c.fork_event, 0));
     } else {
-        const cudaEvent_t deps[3] = {s.used, get_tf(c, s.tf).updated, get_vol(c, s.vol).updated};
-        for (cudaEvent_t e : deps)
-            if (e) ESS_CUDA(cudaStreamWaitEvent(c.build_stream, e, 0));
+        wait_rebuild_deps(c, s, c.build_stream);
     }
-    s.build_pending = true;
-    try {
-        OnStream on(c, c.build_stream);
-        run_build(c, s);
-    } catch (...) {
-        cudaEventRecord(s.built, c.build_stream);
-        throw;
-    }
-    ESS_CUDA(cudaEventRecord(s.built, c.build_stream));
+    build_on(c, s, c.build_stream);
 }
+
+// Streams of ess_rebuild_batch: latency-bound build chains of different
+// structures overlap on them.
+constexpr int BATCH_BUILD_STREAMS = 8;
 
 int64_t nonempty_count(Ctx &c, Structure &s)
 {
@@ -493,7 +519,9 @@ ess_status ess_destroy(ess_ctx *ctx)
         }
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
         if (c.build_stream) cudaStreamDestroy(c.build_stream);
+        for (cudaStream_t st : c.batch_streams) cudaStreamDestroy(st);
         if (c.fork_event) cudaEventDestroy(c.fork_event);
+        if (c.rescan_event) cudaEventDestroy(c.rescan_event);
         cudaFree(c.dev_status);
         cudaFree(c.samples);
         cudaFreeHost(c.host_status);
@@ -708,6 +736,77 @@ ess_status ess_build(ess_ctx *ctx, ess_handle vol, ess_handle tf, ess_kind kind,
         ess_handle h = new_handle(c, TAG_ST);
         c.structures[h] = std::move(s);
         *structure = h;
+    });
+}
+
+ess_status ess_rebuild_batch(ess_ctx *ctx, const ess_handle *structures, int count)
+{
+    return guard(ctx, [&](Ctx &c) {
+        ESS_REQUIRE(structures, "null pointer");
+        ESS_REQUIRE(count >= 1 && count <= 4096, "count must be in 1..4096");
+        std::vector<Structure *> sts;
+        for (int i = 0; i < count; ++i) {
+            Structure &s = get_st(c, structures[i]);
+            ESS_REQUIRE(std::find(sts.begin(), sts.end(), &s) == sts.end(),
+                        "a structure appears twice in the batch");
+            sts.push_back(&s);
+        }
+        ensure_build_stream(c);
+        if (c.batch_streams.empty()) {
+            int least = 0, greatest = 0;
+            ESS_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            for (int k = 0; k < BATCH_BUILD_STREAMS; ++k) {
+                cudaStream_t st;
+                ESS_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest));
+                c.batch_streams.push_back(st);
+            }
+            ESS_CUDA(cudaEventCreateWithFlags(&c.rescan_event, cudaEventDisableTiming));
+        }
+        // one min/max rescan per (volume, brick size), on the first stream,
+        // after every build enqueued so far (they may still read the old one)
+        std::vector<std::pair<ess_handle, int>> rescans;
+        for (Structure *s : sts) {
+            if (s->kind == ESS_NONE || s->p.rescan != 1 || s->p.empty_test != 0) continue;
+            const std::pair<ess_handle, int> key(s->vol, s->p.brick);
+            if (std::find(rescans.begin(), rescans.end(), key) == rescans.end()) rescans.push_back(key);
+        }
+        cudaStream_t s0 = c.batch_streams[0];
+        if (!rescans.empty()) {
+            ESS_CUDA(cudaEventRecord(c.fork_event, c.build_stream));
+            ESS_CUDA(cudaStreamWaitEvent(s0, c.fork_event, 0));
+            for (cudaStream_t st : c.batch_streams) {
+                if (st == s0) continue;
+                ESS_CUDA(cudaEventRecord(c.fork_event, st));
+                ESS_CUDA(cudaStreamWaitEvent(s0, c.fork_event, 0));
+            }
+            OnStream on(c, s0);
+            for (auto &r : rescans) {
+                Volume &v = get_vol(c, r.first);
+                if (v.updated) ESS_CUDA(cudaStreamWaitEvent(s0, v.updated, 0));
+                minmax_for(c, v, r.second, true);
+            }
+            ESS_CUDA(cudaEventRecord(c.rescan_event, s0));
+        }
+        // the builds, spread over the streams; the rescanned min/max is reused
+        for (size_t i = 0; i < sts.size(); ++i) {
+            Structure &s = *sts[i];
+            if (s.kind == ESS_NONE) {
+                s.tf_version = get_tf(c, s.tf).version;
+                continue;
+            }
+            cudaStream_t st = c.batch_streams[i % c.batch_streams.size()];
+            if (!rescans.empty()) ESS_CUDA(cudaStreamWaitEvent(st, c.rescan_event, 0));
+            wait_rebuild_deps(c, s, st);
+            const int rescan = s.p.rescan;
+            s.p.rescan = 0;
+            try {
+                build_on(c, s, st);
+            } catch (...) {
+                s.p.rescan = rescan;
+                throw;
+            }
+            s.p.rescan = rescan;
+        }
     });
 }
 

@@ -196,6 +196,10 @@ struct Ctx {
     // other structures.
     cudaStream_t build_stream = nullptr;
     cudaEvent_t fork_event = nullptr;
+    // ess_rebuild_batch spreads its structures over these (highest priority
+    // too), after one min/max rescan per volume and brick size on the first.
+    std::vector<cudaStream_t> batch_streams;
+    cudaEvent_t rescan_event = nullptr;
     uint32_t *selftest_flag = nullptr;  // device word of ess_selftest_wait
 
     void *alloc(size_t bytes);

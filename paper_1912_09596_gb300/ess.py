@@ -108,6 +108,7 @@ def _load():
         "ess_tf_update": [vp, h, vp, i, i],
         "ess_build": [vp, h, h, i, P(BuildParams), P(h)],
         "ess_rebuild": [vp, h],
+        "ess_rebuild_batch": [vp, P(h), i],
         "ess_structure_info_get": [vp, h, P(StructureInfo)],
         "ess_structure_read": [vp, h, i, vp, C.c_size_t, P(C.c_size_t)],
         "ess_render": [vp, h, P(Camera), P(RenderParams), i, i, vp, i],
@@ -231,6 +232,11 @@ def ess_build(ctx, vol, tf, kind, params=None):
 
 def ess_rebuild(ctx, structure):
     _check(ctx, lib.ess_rebuild(ctx, structure))
+
+
+def ess_rebuild_batch(ctx, structures):
+    arr = (C.c_uint64 * len(structures))(*structures)
+    _check(ctx, lib.ess_rebuild_batch(ctx, arr, len(structures)))
 
 
 def ess_structure_info_get(ctx, structure):
