@@ -66,3 +66,40 @@ def test_binding_constants_match_header(libpath):
             assert getattr(ess, name) == int(value), name
             found += 1
     assert found >= 20
+
+
+STRUCTS = {  # C typedef in include/ess.h -> ctypes mirror in the binding
+    "ess_build_params": "BuildParams", "ess_camera": "Camera",
+    "ess_render_params": "RenderParams", "ess_render_item": "RenderItem",
+    "ess_server_config": "ServerConfig", "ess_request": "Request",
+    "ess_request_status": "RequestStatus", "ess_tune_result": "TuneResult",
+    "ess_structure_info": "StructureInfo",
+}
+
+
+def test_binding_structs_match_header_layout(libpath, tmp_path):
+    """Size and every field offset of each public struct, as the C compiler
+    lays it out from include/ess.h, equal the binding's ctypes mirror."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    from paper_1912_09596_gb300 import ess
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ess.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in getattr(ess, pyname)._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, pyname in STRUCTS.items():
+        cls = getattr(ess, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
