@@ -188,3 +188,15 @@ def test_skipping_never_changes_shaded_image(ora, ert):
                                               shade=SHADE, dt_ref=dt_ref)
                     assert np.array_equal(bits(ref), bits(got))
                     assert n <= nref
+
+
+def test_gradient_at_the_volume_faces_uses_clamped_neighbours(ora):
+    """At the first and last voxel centres along x the outer neighbour is
+    clamped to the edge voxel (R2), so the central difference of a ramp of
+    slope a is a/2 there and a one voxel further in."""
+    n = 10
+    k, j, i = np.meshgrid(np.arange(6), np.arange(6), np.arange(n), indexing="ij")
+    v = (4 * i + 20).astype(np.float32)
+    vol = ora.OVolume(v, 0.0, 100.0)
+    for x, want in ((0.5, 2.0), (1.5, 4.0), (n - 1.5, 4.0), (n - 0.5, 2.0)):
+        assert np.array_equal(ora.gradient(vol, (x, 3.0, 3.0)), np.float32([want, 0.0, 0.0])), x
