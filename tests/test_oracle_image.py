@@ -284,3 +284,49 @@ def test_skipping_rays_on_brick_planes(ora, axis, B):
     got, _ = ora.render_boxes(vol, otf, cam, W, H, boxes)
     assert np.array_equal(bits(ref), bits(got))
     assert np.any(ref[..., 3] > 0)
+
+
+# ------------------------------------------------------- R6 order, R7 stop
+def test_two_layers_composite_front_to_back(ora):
+    """Two layers along the ray: values 50 (front, z < 8) and 200 (back); the
+    TF gives (c1, a1) at 50, (c2, a2) at 200 and alpha 0 in between, so the one
+    sample on the interface (value 125) adds nothing.  Front-to-back
+    absorption + emission (Sec. 4.1): A = 1 - (1-a1)^16 (1-a2)^15 and
+    C = c1 (1 - (1-a1)^16) + (1-a1)^16 c2 (1 - (1-a2)^15); the back-to-front
+    order would weight the layers the other way."""
+    v = np.full((16, 4, 4), 50, dtype=np.uint8)
+    v[8:] = 200
+    tf = np.zeros((256, 4), dtype=np.float32)
+    c1, a1 = np.float32([0.9, 0.2, 0.1]), np.float32(0.05)
+    c2, a2 = np.float32([0.1, 0.3, 0.8]), np.float32(0.2)
+    tf[50, :3], tf[50, 3] = c1, a1
+    tf[200, :3], tf[200, 3] = c2, a2
+    vol, otf = ora.OVolume(v, 0, 255), ora.OTF(tf)
+    cam = synth.axis_ortho_camera(vol.dims, axis=2, half=(1.0, 1.0), eye_back=8.0)
+    img, nsamp = ora.render_naive(vol, otf, cam, 2, 2, dt=0.5)
+    assert nsamp == 4 * 32
+    T1 = (1.0 - np.float64(a1)) ** 16
+    T2 = (1.0 - np.float64(a2)) ** 15
+    tol = 32 * 8 * 2.0 ** -24
+    assert np.all(np.abs(img[..., 3] - (1.0 - T1 * T2)) <= tol)
+    for ch in range(3):
+        want = c1[ch] * (1.0 - T1) + T1 * c2[ch] * (1.0 - T2)
+        assert np.all(np.abs(img[..., ch] - want) <= tol)
+        back_first = c2[ch] * (1.0 - T2) + T2 * c1[ch] * (1.0 - T1)
+        assert np.all(np.abs(img[..., ch] - back_first) > 100 * tol)
+
+
+def test_early_termination_stops_at_the_first_sample_over_the_threshold(ora):
+    """R7: alpha 0.5 per sample gives A = 1 - 2^-k exactly after k samples;
+    with ert 0.9 every ray stops after its 4th sample (A = 0.9375)."""
+    v = np.full((16, 4, 4), 100, dtype=np.uint8)
+    tf = np.zeros((256, 4), dtype=np.float32)
+    tf[:, 0], tf[:, 3] = 1.0, 0.5
+    vol, otf = ora.OVolume(v, 0, 255), ora.OTF(tf)
+    cam = synth.axis_ortho_camera(vol.dims, axis=2, half=(1.0, 1.0), eye_back=8.0)
+    img, nsamp = ora.render_naive(vol, otf, cam, 2, 2, dt=0.5, ert=0.9)
+    assert nsamp == 4 * 4
+    assert np.all(img[..., 3] == np.float32(0.9375))
+    assert np.all(img[..., 0] == np.float32(0.9375))
+    img, nsamp = ora.render_naive(vol, otf, cam, 2, 2, dt=0.5, ert=0.9375)
+    assert nsamp == 4 * 4                         # A >= ert at the 4th sample
