@@ -20,3 +20,13 @@ def test_ct512_recipe_occupancy_and_determinism(ora):
     assert len(occ) == 8
     assert all(0.05 <= o <= 0.30 for o in occ), occ
     assert max(occ) - min(occ) > 0.1          # the edits really change the empty space
+
+
+def test_blobs64_recipe_occupancy():
+    """The small case (64^3 blobs, TF alpha 0 below 40 and a ramp above):
+    about 10 % of the voxels are visible."""
+    v = synth.blobs_u8((64, 64, 64), seed=0)
+    frac = float((v >= 40).mean())
+    assert 0.05 <= frac <= 0.2, frac
+    tf = synth.tf_ramp(256, 40)
+    assert np.all(tf[:40, 3] == 0) and np.all(tf[41:, 3] > 0)
