@@ -195,3 +195,23 @@ def test_shallow_halting_is_strict(ora):
     eq = [i for i in range(len(nodes)) if 10 * vol_of(nodes[i, :6].tolist(), B, dims) == vroot]
     assert eq and all(nodes[i, 8] == -1 for i in eq)
     check_tree(nodes, mask, grid, B, dims, 0, 0, 0)
+
+
+@pytest.mark.parametrize("nbins", [0, 4])
+def test_two_clusters_split_in_the_gap_by_hand(ora, nbins):
+    """A hand-derived tree (R9, Sec. 3.2.1): two 2x2x2-brick clusters in
+    opposite corners of an 8^3-brick grid.  Every plane inside the gap, on
+    any axis, gives the two clusters' boxes as L and R (the least cost), so
+    the tie rule picks axis x and the lowest such plane, 2 (a candidate with
+    and without 4 bins).  A full 2x2x2 cube cannot lower its cost by any
+    split (V(L) + V(R) = V), so both children are leaves: 3 nodes."""
+    g = 8
+    mask = np.zeros((g, g, g), dtype=np.uint8)       # [z][y][x]
+    mask[:2, :2, :2] = 1
+    mask[6:, 6:, 6:] = 1
+    B = 8
+    nodes = ora.kd_build(mask.reshape(-1), (g, g, g), B, (g * B,) * 3, nbins=nbins, halting=1, mls=0)
+    want = np.array([[0, 0, 0, 8, 8, 8, 0, 2, 1],
+                     [0, 0, 0, 2, 2, 2, -1, 0, -1],
+                     [6, 6, 6, 8, 8, 8, -1, 0, -1]], dtype=np.int32)
+    assert np.array_equal(nodes, want)
