@@ -38,8 +38,9 @@
  *     bound, complete-tree case, containment and separation;
  *   k-d: invariants, per-node brute-force argmin, Table 1 "Menger sponge,
  *     shallow: 1 node, height 1".  The greedy topology itself has no printed
- *     value to compare with; a hand-derived two-cluster tree pins the choice
- *     and tie rules; beyond that, parity unpinned.
+ *     value to compare with; hand-derived trees (two corner clusters; a full
+ *     cube under the maximum leaf size) pin the choice, tie and MLS rules;
+ *     beyond that, parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>

@@ -215,3 +215,24 @@ def test_two_clusters_split_in_the_gap_by_hand(ora, nbins):
                      [0, 0, 0, 2, 2, 2, -1, 0, -1],
                      [6, 6, 6, 8, 8, 8, -1, 0, -1]], dtype=np.int32)
     assert np.array_equal(nodes, want)
+
+
+@pytest.mark.parametrize("nbins", [0, 4])
+def test_full_cube_max_leaf_size_by_hand(ora, nbins):
+    """A hand-derived tree for the maximum leaf size (Sec. 4.3, R9): a full
+    8^3-brick cube (64^3 voxels) never lowers its cost by a split (L and R
+    always fill V), so only the MLS 32 rule splits it: in the middle of the
+    longest axis, the lower axis on ties, until the 32^3-voxel octants."""
+    g, B = 8, 8
+    mask = np.ones((g, g, g), dtype=np.uint8)
+    nodes = ora.kd_build(mask.reshape(-1), (g, g, g), B, (g * B,) * 3, nbins=nbins, halting=1, mls=32)
+    want = [[0, 0, 0, 8, 8, 8, 0, 4, 1],
+            [0, 0, 0, 4, 8, 8, 1, 4, 3], [4, 0, 0, 8, 8, 8, 1, 4, 5],
+            [0, 0, 0, 4, 4, 8, 2, 4, 7], [0, 4, 0, 4, 8, 8, 2, 4, 9],
+            [4, 0, 0, 8, 4, 8, 2, 4, 11], [4, 4, 0, 8, 8, 8, 2, 4, 13]]
+    for lo in [(0, 0, 0), (0, 0, 4), (0, 4, 0), (0, 4, 4), (4, 0, 0), (4, 0, 4), (4, 4, 0), (4, 4, 4)]:
+        want.append([lo[0], lo[1], lo[2], lo[0] + 4, lo[1] + 4, lo[2] + 4, -1, 0, -1])
+    assert np.array_equal(nodes, np.array(want, dtype=np.int32))
+    # without the maximum leaf size the cube stays one leaf
+    one = ora.kd_build(mask.reshape(-1), (g, g, g), B, (g * B,) * 3, nbins=nbins, halting=1, mls=0)
+    assert np.array_equal(one, np.array([[0, 0, 0, 8, 8, 8, -1, 0, -1]], dtype=np.int32))
