@@ -1109,7 +1109,7 @@ def run_ours(args, rank, local, ws, dist):
         print(json.dumps(result))
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -1133,7 +1133,11 @@ def main():
                     help="skip the shaded-render workload (gradient shading, opacity correction)")
     ap.add_argument("--no-structures", action="store_true",
                     help="skip the structure comparison (node counts, heights, build and frame times)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     rank, local, ws, dist = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank)
