@@ -1,6 +1,7 @@
 """Parity at the benchmark's full sizes, on outputs the oracle can compute
-one by one: the brick masks of the 512^3 CT-like workload (every brick),
-and sampled pixels of full frames rendered in the benchmark's launch
+one by one: the brick masks of the 512^3 CT-like workload (every brick), the
+whole trees that the benchmark step builds for its eight TF edits (k-d node
+records and LBVH topology and boxes, bit for bit), and sampled pixels of full frames rendered in the benchmark's launch
 configuration (512^3 u8 at 1024^2, 1024^3 f32 at 1920x1080), each checked
 against the oracle's naive marching of that pixel."""
 import math
@@ -65,6 +66,71 @@ def test_ct512_masks_and_sampled_pixels(gpu, ctx, ora, ct512):
             _check_pixels(out.cpu().numpy(), xy, ref, "ct512 TF %d %s" % (ti, ess.KIND_NAMES[kind]))
             ess.ess_release(ctx, st)
         ess.ess_release(ctx, t)
+
+
+def _tree_arrays(ess, ctx, st, kind):
+    rd = lambda a: ess.ess_structure_read(ctx, st, a)
+    if kind == ess.LBVH:
+        return dict(ids=rd(ess.ARR_IDS), keys=rd(ess.ARR_KEYS), sorted_keys=rd(ess.ARR_SORTED_KEYS),
+                    sorted_ids=rd(ess.ARR_SORTED_IDS), left=rd(ess.ARR_LBVH_LEFT),
+                    right=rd(ess.ARR_LBVH_RIGHT), boxes=rd(ess.ARR_LBVH_BOXES).reshape(-1, 6))
+    return dict(nodes=rd(ess.ARR_KD_NODES).reshape(-1, 9))
+
+
+# (brick, kind, k-d parameters): the benchmark step's structures at 8^3 bricks
+# (deep binned k-d with maximum leaf 32^3, Sec. 4.3), its hybrid's shallow tree,
+# and the other brick sizes of the 512^3 workload.
+TREES = [(8, "lbvh", None), (8, "kd", dict(nbins=4, halting=1, mls=32)),
+         (8, "kd", dict(nbins=4, halting=0, mls=0)), (16, "lbvh", None),
+         (16, "kd", dict(nbins=4, halting=1, mls=32)), (32, "lbvh", None),
+         (32, "kd", dict(nbins=4, halting=1, mls=128))]
+
+
+def test_ct512_trees_bit_exact(gpu, ctx, ora, ct512):
+    """Every TF edit of the 512^3 workload: the trees rebuilt with a min/max
+    rescan, exactly as the timed step builds them, equal the oracle's builds on
+    the oracle's masks (Sec. 3.1 LBVH, Sec. 3.2.2 binned k-d): Morton keys, sort
+    order, Karras children and boxes; k-d boxes, axes, planes and children."""
+    ess, torch = gpu
+    vol_np, tfs, _ = ct512
+    ov = ora.OVolume(vol_np, 0, 255)
+    mm = {B: ora.brick_minmax(ov, B) for B in (8, 16, 32)}
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).cuda(), 0, 255)
+    t = ess.ess_tf_set(ctx, torch.from_numpy(tfs[0]).cuda())
+    structs = []
+    for B, name, kp in TREES:
+        kind = ess.LBVH if name == "lbvh" else ess.KD
+        structs.append((B, name, kp, kind,
+                        ess.ess_build(ctx, vol, t, kind,
+                                      ess.build_params(brick=B, rescan=1, **(kp or {})))))
+    nodes_seen = 0
+    for ti, tf in enumerate(tfs):
+        ot = ora.OTF(tf)
+        if ti > 0:
+            ess.ess_tf_update(ctx, t, torch.from_numpy(tf).cuda())
+            for *_, st in structs:
+                ess.ess_rebuild(ctx, st)
+        for B, name, kp, kind, st in structs:
+            mask = ora.brick_mask(mm[B][0], mm[B][1], ot, 0, 255)
+            got = _tree_arrays(ess, ctx, st, kind)
+            what = "TF %d B %d %s %s" % (ti, B, name, kp)
+            if kind == ess.LBVH:
+                ref = ora.lbvh_build(mask, ov.grid(B))
+                for key in got:
+                    assert np.array_equal(got[key], ref[key].reshape(got[key].shape)), \
+                        "%s: %s differs" % (what, key)
+                n = len(ref["ids"])
+                assert ess.ess_structure_info_get(ctx, st)["n_nodes"] == (2 * n - 1 if n else 0)
+                nodes_seen += 2 * n - 1
+            else:
+                ref = ora.kd_build(mask, ov.grid(B), B, ov.dims, **kp)
+                assert got["nodes"].shape == ref.shape, (what, got["nodes"].shape, ref.shape)
+                assert np.array_equal(got["nodes"], ref), what + ": k-d nodes differ"
+                assert ess.ess_structure_info_get(ctx, st)["n_nodes"] == len(ref)
+                nodes_seen += len(ref)
+    assert nodes_seen > 500000   # whole trees of thousands of nodes, not toy cases
+    for *_, st in structs:
+        ess.ess_release(ctx, st)
 
 
 def test_fractal1024_f32_mask_and_sampled_pixels(gpu, ctx, ora):
