@@ -47,6 +47,11 @@ WORKLOADS = {
              "8 TF edits with 5-30% non-empty 8^3 bricks; rebuild per edit; "
              "1024x1024 perspective, dt 0.5 voxel, ERT 0.99",
         dims=(512, 512, 512), W=1024, H=1024, dt=0.5, ert=0.99, brick=8),
+    "fractal1024": dict(
+        desc="1024^3 float32 fractal field (4 octaves of value noise, thresholded: 1-5% "
+             "non-empty 8^3 bricks), 1024-entry TF; one TF upload and rebuild of every "
+             "structure, then 16 orbit views at 1920x1080 perspective, dt 0.5 voxel, no ERT",
+        dims=(1024, 1024, 1024), W=1920, H=1080, dt=0.5, ert=2.0, brick=8),
     "blobs64": dict(
         desc="64^3 uint8 Gaussian blobs, TF ramp from 40, brick 8^3, 256x256 perspective, "
              "dt 0.5, no ERT", dims=(64, 64, 64), W=256, H=256, dt=0.5, ert=2.0, brick=8),
@@ -54,26 +59,54 @@ WORKLOADS = {
 KD_PARAMS = dict(nbins=4, halting=1, mls=32)   # GPU k-d, deep, maximum leaf 32^3 (Sec. 4.3)
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
-SMS, FP32_LANES_PER_SM = 152, 128
+FP32_LANES_PER_SM = 128
 # FP32 operations of one evaluated sample as the method defines it (FMA = 2):
 # position 3 FMA (6); cell weights 3 floor + 3 sub (6); trilinear 7 x (sub +
 # FMA) (21); TF coordinate FMA + 2 clamps + floor + sub (6); TF lerp 4 x (sub +
 # FMA) (12); compositing sub, mul, 3 FMA, add (9); termination compare (1).
 FLOP_PER_SAMPLE = 61
 
+# The bench.py argument lists of the runs that the summaries under profiles/
+# were captured from (each summary names its entry); a CPU test parses them all.
+PROFILE_COMMANDS = {
+    "step_ct512": "--steps 1 --warmup 1 --no-cpu-baseline --no-batched --no-serve --no-minmax "
+                  "--no-hybrid --no-structures --no-shaded --no-cell-vote --no-fractal",
+    "step_ct512_shaded": "--steps 1 --warmup 1 --no-cpu-baseline --no-batched --no-serve "
+                         "--no-minmax --no-hybrid --no-structures --no-cell-vote --no-fractal",
+    "step_ct512_hybrid": "--steps 1 --warmup 1 --no-cpu-baseline --no-batched --no-serve "
+                         "--no-minmax --no-structures --no-shaded --no-cell-vote --no-fractal",
+    "step_ct512_vote_batch": "--steps 1 --warmup 1 --no-cpu-baseline --no-serve --no-minmax "
+                             "--no-hybrid --no-structures --no-shaded --no-fractal",
+    "step_fractal1024": "--workload fractal1024 --steps 1 --warmup 1 --no-cpu-baseline",
+    "bench_default": "",
+}
 
-def make_inputs(name):
+
+def make_inputs(name, dev=None):
+    """Volume (numpy, or a torch tensor for the 1024^3 field), value range,
+    the TF tables of the edits and, per edit, the cameras rendered after it."""
     from paper_1912_09596_gb300 import synth
     w = WORKLOADS[name]
+    if name == "fractal1024":
+        vol = synth.fractal_f32_torch(w["dims"], seed=2, device=dev if dev is not None else "cpu")
+        tfs = [synth.tf_ramp(1024, 2)]
+        views = [[synth.orbit_camera(w["dims"], w["W"], w["H"], theta=2 * math.pi * k / 16,
+                                     phi=0.35, dist=1.6) for k in range(16)]]
+        return vol, (0.0, 1.0), tfs, views
     if name == "ct512":
         vol = synth.ct_like_u8(w["dims"], seed=1)
         tfs = synth.tf_set_ct(256)
     else:
         vol = synth.blobs_u8(w["dims"], seed=0)
         tfs = [synth.tf_ramp(256, 40) for _ in range(8)]
-    cams = [synth.orbit_camera(w["dims"], w["W"], w["H"], theta=2 * math.pi * i / len(tfs),
-                               phi=0.35, dist=1.6) for i in range(len(tfs))]
-    return vol, (0.0, 255.0), tfs, cams
+    views = [[synth.orbit_camera(w["dims"], w["W"], w["H"], theta=2 * math.pi * i / len(tfs),
+                                 phi=0.35, dist=1.6)] for i in range(len(tfs))]
+    return vol, (0.0, 255.0), tfs, views
+
+
+def host_array(vol):
+    """The volume as a host numpy array (the oracle's input)."""
+    return vol if isinstance(vol, np.ndarray) else vol.cpu().numpy()
 
 
 # ---------------------------------------------------------------- clocks
@@ -138,16 +171,16 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def fp32_peak_tflops():
-    """FP32 roof from unit counts and the maximum SM clock: 152 SMs x 128 FP32
-    lanes x 2 FLOP per FMA x clock."""
+def fp32_peak_tflops(sms):
+    """FP32 roof from unit counts and the maximum SM clock: the device's SMs x
+    128 FP32 lanes x 2 FLOP per FMA x clock."""
     mhz = 2070.0
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             mhz = float(json.load(f).get("sm_max_mhz", mhz))
     except (OSError, ValueError):
         pass
-    return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, mhz
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, mhz
 
 
 # source files that define each kernel (by profiling-name prefix); every
@@ -155,7 +188,7 @@ def fp32_peak_tflops():
 KERNEL_FILES = (("render_shaded", ("render_shaded.cu", "render_kernels.h")),
                 ("render", ("render.cu", "render_kernels.h")), ("brick_", ("classify.cu",)),
                 ("compact", ("classify.cu",)), ("tf_prefix", ("classify.cu",)),
-                ("mask_cells", ("classify.cu",)), ("build_cells", ("classify.cu",)),
+                ("vote_bricks", ("classify.cu",)), ("build_cells", ("classify.cu",)),
                 ("check_finite", ("classify.cu",)), ("sort", ("lbvh.cu",)),
                 ("lbvh", ("lbvh.cu",)), ("kd", ("kd.cu",)))
 
@@ -252,15 +285,17 @@ def run_reference(args, rank):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
-    vol, (vlo, vhi), tfs, cams = make_inputs(args.workload)
+    vol, (vlo, vhi), tfs, views = make_inputs(args.workload)
+    vol = host_array(vol)
+    cams = [(tfs[i], c) for i, vs in enumerate(views) for c in vs]
     cores = cpu_cores()
     for _ in range(args.warmup):
-        oracle_rate(vol, vlo, vhi, tfs[0], cams[0], w, 0.2, cores)
+        oracle_rate(vol, vlo, vhi, cams[0][0], cams[0][1], w, 0.2, cores)
     rates, descs, t_all = [], [], 0.0
     for k in range(args.steps):
-        i = k % len(tfs)
+        tf_k, cam_k = cams[k % len(cams)]
         t0 = time.perf_counter()
-        r, d = oracle_rate(vol, vlo, vhi, tfs[i], cams[i], w, args.ref_budget, cores)
+        r, d = oracle_rate(vol, vlo, vhi, tf_k, cam_k, w, args.ref_budget, cores)
         t_all += time.perf_counter() - t0
         rates.append(r)
         descs.append(d)
@@ -279,8 +314,9 @@ def run_reference(args, rank):
     print(json.dumps(out))
 
 
-METRIC = ("ray samples/s (naive-equivalent) over TF edit + rebuild + render of grid, "
-          "LBVH and k-d structures")
+METRIC = ("ray samples/s, naive-equivalent (per frame, the samples the non-skipping marcher "
+          "takes; the samples the skipping renderers evaluate are in evaluated_samples_per_s), over "
+          "TF edit + rebuild + render of grid, LBVH and k-d structures")
 
 BATCH_SIZES = [(256, 256), (512, 512), (1024, 1024), (1920, 1080)]
 
@@ -539,12 +575,12 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=3.0):
         return st, t_sub, span
 
     # plain and served alternate REPS times at the same arrival times; each
-    # arm reports its repetition of median throughput (the host is shared, so
+    # arm reports its repetition of median throughput and the spread (the host is shared, so
     # a single repetition can catch a stall of either arm, the plain loop's
     # more often: it waits for every request).  Clocks are
     # sampled before and after the repetitions, not during them: an
     # nvidia-smi query can hold up these host-driven request loops.
-    REPS = 5
+    REPS = 7
 
     def clock_snapshot():
         sampler = ClockSampler(torch.cuda.current_device())
@@ -571,6 +607,9 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=3.0):
     med = lambda runs: sorted(runs, key=lambda x: x[0])[len(runs) // 2]
     fps_plain, lat_plain = med(plain_runs)
     fps_served, st, t_sub = med(served_runs)
+    spread = lambda runs: {"min": round(min(r[0] for r in runs), 1),
+                           "median": round(med(runs)[0], 1),
+                           "max": round(max(r[0] for r in runs), 1)}
     lat_served = [x["latency_ms"] for x in st]
     queue_ms = [x["queue_ms"] for x in st]
     # requests issued together share one launch time
@@ -585,13 +624,13 @@ def run_served(ess, torch, dev, ctx, ct512, n_req=240, load=3.0):
         "requests": n_req, "rate_hz": round(lam, 2), "serial_service_rate_hz": round(mu, 2),
         "repetitions": REPS,
         "plain": {"frames_per_s": fps_plain, "p50_ms": pct(lat_plain, 50),
-                  "p99_ms": pct(lat_plain, 99),
+                  "p99_ms": pct(lat_plain, 99), "frames_per_s_spread": spread(plain_runs),
                   "frames_per_s_all": [round(r[0], 1) for r in plain_runs]},
         "served": {"frames_per_s": fps_served, "p50_ms": pct(lat_served, 50),
                    "p99_ms": pct(lat_served, 99), "all_ok": ok,
                    "mean_queue_ms": float(np.mean(queue_ms)),
                    "mean_service_ms": float(np.mean(np.subtract(lat_served, queue_ms))),
-                   "batches": len(launches),
+                   "batches": len(launches), "frames_per_s_spread": spread(served_runs),
                    "frames_per_s_all": [round(r[0], 1) for r in served_runs]},
         "bit_identical_to_plain": bool(same),
         "clocks": clk,
@@ -638,51 +677,64 @@ def run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, steps=3):
 def run_cell_vote(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, B, vox_bytes, reps=3):
     """The exact per-cell vote (the paper's per-voxel classification, Sec.
     3.1) against the brick min/max range test on the main workload's TF
-    edits: time of the per-cell mask kernel (it reads the volume once per edit)
-    against the measured HBM peak, the non-empty fraction of each mask (the
-    vote's is a subset of the range test's), and the grid frame through each."""
+    edits.  Both read the volume once per edit (the min/max pass); the vote
+    then tests the cells of the bricks the range test passes.  Reported: each
+    path's empty-test time per edit (its kernels' CUDA-event times) and its
+    rate on the volume's bytes against the measured HBM peak, the non-empty
+    fraction of each mask (the vote's is a subset of the range test's), and
+    the grid frame through each."""
     peak, src = measured_peaks()
     out = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
-    vote = ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, empty_test=1))
-    rng = ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, rescan=1))
-    frac = {"vote": [], "minmax": []}
-    for i in range(len(tf_dev)):   # warm-up and mask sizes
-        ess.ess_tf_update(ctx, tf, tf_dev[i])
-        for name, st in (("vote", vote), ("minmax", rng)):
-            ess.ess_rebuild(ctx, st)
-            info = ess.ess_structure_info_get(ctx, st)
-            frac[name].append(info["n_nonempty"] / info["n_bricks"])
-    ess.ess_sync(ctx)
-    ess.ess_profile_reset(ctx)
-    ess.ess_profile_enable(ctx, True)
+    paths = {"vote": ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, empty_test=1,
+                                                                            rescan=1)),
+             "minmax": ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, rescan=1))}
+    frac = {k: [] for k in paths}
+    test_ms = {k: [] for k in paths}
+    vote_ms = []
+    frame = {k: [] for k in paths}
     cur = torch.cuda.current_stream()
-    frame = {"vote": [], "minmax": []}
-    for _ in range(reps):
+    for rep in range(reps + 1):          # the first pass warms up
         for i in range(len(tf_dev)):
-            ess.ess_tf_update(ctx, tf, tf_dev[i])
-            for name, st in (("vote", vote), ("minmax", rng)):
+            for name, st in paths.items():
+                ess.ess_tf_update(ctx, tf, tf_dev[i])   # an edit: the volume pass runs again
+                ess.ess_sync(ctx)
+                ess.ess_profile_reset(ctx)
+                ess.ess_profile_enable(ctx, True)
                 ess.ess_rebuild(ctx, st)
                 ess.ess_sync(ctx)
+                ess.ess_profile_enable(ctx, False)
+                prof = ess.ess_profile_read(ctx)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(cur)
                 ess.ess_render(ctx, st, ecams[i], rp, W, H, out)
                 b.record(cur)
                 b.synchronize()
+                if rep == 0:
+                    info = ess.ess_structure_info_get(ctx, st)
+                    frac[name].append(info["n_nonempty"] / info["n_bricks"])
+                    continue
+                test_ms[name].append(sum(prof.get(k, (0, 0.0))[1] for k in
+                                         ("brick_minmax", "brick_mask", "vote_bricks")))
+                if name == "vote":
+                    vote_ms.append(prof["vote_bricks"][1])
                 frame[name].append(a.elapsed_time(b))
-    ess.ess_profile_enable(ctx, False)
-    prof = ess.ess_profile_read(ctx)
-    ess.ess_release(ctx, vote)
-    ess.ess_release(ctx, rng)
-    n, ms = prof["mask_cells"]
-    nvox = vox_bytes
-    gbs = nvox / (ms / n / 1000.0) / 1e9
-    return {"workload": "the main workload's 8 TF edits, grid structure at %d^3 bricks" % B,
-            "mask_cells_us": round(1000.0 * ms / n, 2),
-            "mask_cells_hbm": {"achieved_gbs": round(gbs, 1), "peak_gbs": peak, "peak_source": src,
-                               "frac": round(gbs / peak, 3),
-                               "algorithmic_bytes": "the volume once"},
-            "nonempty_fraction": {k: [round(x, 4) for x in v] for k, v in frac.items()},
-            "grid_frame_ms": {k: round(float(np.mean(v)), 4) for k, v in frame.items()},
+    for st in paths.values():
+        ess.ess_release(ctx, st)
+    res = {}
+    for name in paths:
+        ms = float(np.mean(test_ms[name]))
+        gbs = vox_bytes / (ms / 1000.0) / 1e9
+        res[name] = {"empty_test_us_per_edit": round(1000.0 * ms, 2),
+                     "hbm_on_volume_bytes": {"achieved_gbs": round(gbs, 1), "peak_gbs": peak,
+                                             "peak_source": src, "frac": round(gbs / peak, 3)},
+                     "nonempty_fraction": [round(x, 4) for x in frac[name]],
+                     "grid_frame_ms": round(float(np.mean(frame[name])), 4)}
+    return {"workload": "the main workload's 8 TF edits, grid structure at %d^3 bricks, one "
+                        "volume pass (min/max) per edit on both paths" % B,
+            "vote_bricks_us": round(1000.0 * float(np.mean(vote_ms)), 2),
+            "kernels": {"vote": "brick_minmax + brick_mask + vote_bricks",
+                        "minmax": "brick_minmax + brick_mask"},
+            **res,
             "note": "the vote's mask is never larger than the range test's, and the images are "
                     "the same"}
 
@@ -750,10 +802,14 @@ def run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, reps=
         ess.ess_release(ctx, g)
     picks = sorted({int(np.argmin(nonempty)), int(np.argmax(nonempty))})
     rows = []
+    runs = [(8,) + c for c in configs]
+    for B in (16, 32):
+        runs += [(B, "grid", ess.GRID, {}), (B, "lbvh", ess.LBVH, {}),
+                 (B, "kd_binned_deep_mls32", ess.KD, dict(KD_PARAMS))]
     for i in picks:
         ess.ess_tf_update(ctx, tf, tf_dev[i])
-        for name, kind, prm in configs:
-            st = ess.ess_build(ctx, vol, tf, kind, ess.build_params(brick=8, **prm))
+        for B, name, kind, prm in runs:
+            st = ess.ess_build(ctx, vol, tf, kind, ess.build_params(brick=B, **prm))
             ess.ess_render(ctx, st, ecams[i], rp, W, H, out)   # warm
             ess.ess_sync(ctx)
             ess.ess_profile_reset(ctx)
@@ -767,13 +823,15 @@ def run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H, reps=
             info = ess.ess_structure_info_get(ctx, st)
             render = sum(v[1] for k, v in prof.items() if k.startswith("render")) / reps
             build = sum(v[1] for k, v in prof.items() if not k.startswith("render")) / reps
-            rows.append({"tf_edit": i, "nonempty_bricks": int(nonempty[i]), "structure": name,
-                         "nodes": int(info["n_nodes"]), "height": int(info["height"]),
-                         "build_ms": round(build, 4), "frame_ms": round(render, 4)})
+            rows.append({"tf_edit": i, "nonempty_bricks": int(info["n_nonempty"]),
+                         "structure": name, "brick": B, "nodes": int(info["n_nodes"]),
+                         "height": int(info["height"]), "build_ms": round(build, 4),
+                         "frame_ms": round(render, 4)})
             ess.ess_release(ctx, st)
-    return {"workload": "the main workload (512^3 CT-like, 8^3 bricks, 1024^2 frame), sparsest and "
-                        "densest of its TF edits; build = one rebuild (min/max cached), frame = one "
-                        "render, CUDA-event means of %d" % reps, "rows": rows}
+    return {"workload": "the main workload (512^3 CT-like, 1024^2 frame), sparsest and densest of "
+                        "its TF edits; every structure at 8^3 bricks, the step's three at 16^3 and "
+                        "32^3 too; build = one rebuild (min/max cached), frame = one render, "
+                        "CUDA-event means of %d" % reps, "rows": rows}
 
 
 def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
@@ -801,18 +859,22 @@ def run_minmax_sweep(ess, torch, dev, ctx, reps=10):
             lo, hi = 0.0, 1.0
         vol = ess.ess_volume_upload(ctx, x, lo, hi)
         ess.ess_volume_set_sampler(ctx, vol, 0)
-        tf = ess.ess_tf_set(ctx, synth.tf_ramp(256, 40))
+        tf_np = synth.tf_ramp(256, 40)
+        tf = ess.ess_tf_set(ctx, tf_np)
         for B in (8, 16, 32):
             st = ess.ess_build(ctx, vol, tf, ess.GRID, ess.build_params(brick=B, rescan=1))
             for _ in range(2):
+                ess.ess_tf_update(ctx, tf, tf_np)
                 ess.ess_rebuild(ctx, st)
             ess.ess_sync(ctx)
             ess.ess_profile_reset(ctx)
             ess.ess_profile_enable(ctx, True)
             for _ in range(reps):
-                # the rebuild runs on the library's build stream, which does not
-                # wait for this stream: finish the flush first, and the rebuild
-                # before the next flush
+                # a TF edit (the same table again): the rebuild reads the volume
+                # once more.  The rebuild runs on the library's build stream,
+                # which does not wait for this stream: finish the flush first,
+                # and the rebuild before the next flush
+                ess.ess_tf_update(ctx, tf, tf_np)
                 flush.zero_()
                 torch.cuda.synchronize(dev)
                 ess.ess_rebuild(ctx, st)
@@ -850,6 +912,278 @@ PAPER_TABLE2_512 = {
 }
 
 
+def measure_step(ess, torch, dev, stream, ctx, name, steps, warmup, dist=None, ws=1,
+                 e2e=True, sample_clocks=True, inputs=None):
+    """Times `steps` passes of the hot path over workload `name` (after
+    `warmup` untimed ones) inside the library's context `ctx`: per TF edit the
+    table upload, the rebuild of the grid, LBVH and k-d structures with a
+    min/max rescan (one volume pass per edit, shared by the three), then one
+    frame through each structure for every view of that edit.  Returns (the
+    bench line's measurement fields, the resident objects for further legs)."""
+    w = WORKLOADS[name]
+    vol_in, (vlo, vhi), tfs_np, views = inputs if inputs is not None else make_inputs(name, dev)
+    W, H, B = w["W"], w["H"], w["brick"]
+    kinds = [k for k in ess.KINDS if k != ess.NONE]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    data = vol_in.to(dev) if hasattr(vol_in, "to") else torch.from_numpy(vol_in).to(dev)
+    itemsize = data.element_size()
+    nvox = data.numel()
+    vshape = tuple(data.shape)
+    vol = ess.ess_volume_upload(ctx, data, vlo, vhi)
+    del data
+    tf_dev = [torch.from_numpy(t).to(dev) for t in tfs_np]
+    tf_host = [torch.from_numpy(t).pin_memory() for t in tfs_np]
+    tf = ess.ess_tf_set(ctx, tf_dev[0])
+    # rescan: the first rebuild of each edit recomputes the brick min/max from
+    # the voxels, and the other structures of the edit reuse it
+    params = {k: ess.build_params(brick=B, rescan=1, **KD_PARAMS) for k in kinds}
+    st = {k: ess.ess_build(ctx, vol, tf, k, params[k]) for k in kinds}
+    naive = ess.ess_build(ctx, vol, tf, ess.NONE)
+    outs = {k: torch.empty((H, W, 4), dtype=torch.float32, device=dev) for k in kinds}
+    host_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rp = ess.render_params(w["dt"], w["ert"])
+    ecams = [[ess.camera_from(c) for c in vs] for vs in views]
+    frames_step = sum(len(vs) for vs in views) * len(kinds)
+
+    # per-frame reference counts (untimed): naive samples, evaluated samples,
+    # non-empty bricks, algorithmic bytes of each render, naive frame time
+    n_naive, n_eval = [], {k: [] for k in kinds}
+    alg_bytes, nonempty = {k: [] for k in kinds}, []
+    naive_ms = []
+    cur = torch.cuda.current_stream(dev)
+    for i in range(len(tfs_np)):
+        ess.ess_tf_update(ctx, tf, tf_dev[i])
+        ess.ess_rebuild(ctx, naive)
+        for k in kinds:
+            ess.ess_rebuild(ctx, st[k])
+        infos = {k: ess.ess_structure_info_get(ctx, st[k]) for k in kinds}
+        nonempty.append(infos[kinds[0]]["n_nonempty"] / max(1, infos[kinds[0]]["n_bricks"]))
+        for cam in ecams[i]:
+            ess.ess_sync(ctx)
+            ess.ess_sample_count(ctx, reset=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(cur)
+            ess.ess_render(ctx, naive, cam, rp, W, H, outs[kinds[0]])
+            b.record(cur)
+            n_naive.append(ess.ess_sample_count(ctx, reset=True))
+            naive_ms.append(a.elapsed_time(b))
+            for k in kinds:
+                ess.ess_render(ctx, st[k], cam, rp, W, H, outs[k])
+                n_eval[k].append(ess.ess_sample_count(ctx, reset=True))
+                info = infos[k]
+                # compulsory bytes of one frame: the image, the voxels of the
+                # non-empty bricks and the structure itself
+                struct_b = info["n_bricks"] if k == ess.GRID else 32 * max(1, info["n_nodes"])
+                alg_bytes[k].append(W * H * 16 + info["n_nonempty"] * B ** 3 * itemsize + struct_b)
+    ess.ess_sync(ctx)
+
+    def step(host_io=False):
+        # the library runs the rebuilds on its build stream: the k-d and LBVH
+        # rebuilds overlap the grid's frame
+        for i in range(len(tfs_np)):
+            ess.ess_tf_update(ctx, tf, tf_host[i] if host_io else tf_dev[i])
+            for k in kinds:
+                ess.ess_rebuild(ctx, st[k])
+            for cam in ecams[i]:
+                for k in kinds:
+                    ess.ess_render(ctx, st[k], cam, rp, W, H, host_out if host_io else outs[k])
+
+    for _ in range(warmup):
+        step()
+    ess.ess_sync(ctx)
+    launches0 = ess.ess_launch_count(ctx)
+    ess.ess_profile_reset(ctx)
+    ess.ess_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0) if sample_clocks else None
+    for s_ in range(steps):
+        flush.zero_()                        # L2 flush between timed steps (untimed)
+        ev[s_][0].record(stream)
+        step()
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    launches = ess.ess_launch_count(ctx) - launches0
+    ess.ess_profile_enable(ctx, False)
+    prof = ess.ess_profile_read(ctx)
+    ess.ess_sync(ctx)
+    t_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev), dev)
+
+    e2e_ms = None
+    if e2e:
+        # end to end through the ABI with host buffers
+        for _ in range(max(1, warmup // 2)):
+            step(host_io=True)
+        ess.ess_sync(ctx)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step(host_io=True)
+        ess.ess_sync(ctx)
+        e2e_ms = max_over_ranks(dist, 1000.0 * (time.perf_counter() - t0), dev)
+
+    # the step's rebuilds alone (no frame beside them): per edit, the TF
+    # upload and the three rebuilds, waited for before the next edit
+    ess.ess_profile_reset(ctx)
+    ess.ess_profile_enable(ctx, True)
+    for _ in range(steps):
+        for i in range(len(tfs_np)):
+            ess.ess_tf_update(ctx, tf, tf_dev[i])
+            for k in kinds:
+                ess.ess_rebuild(ctx, st[k])
+            ess.ess_sync(ctx)
+    ess.ess_profile_enable(ctx, False)
+    prof_alone = ess.ess_profile_read(ctx)
+
+    units_step = sum(n_naive) * len(kinds)
+    evaluated_step = sum(sum(v) for v in n_eval.values())
+    value = job_rate(units_step, ws, steps, t_ms)
+
+    # dominant kernel and its roofline on algorithmic bytes (among the renders:
+    # the build kernels run on the build stream alongside them, so their event
+    # intervals include the time they share the GPU with a render)
+    kind_of = {"render_grid": ess.GRID, "render_lbvh": ess.LBVH, "render_kd": ess.KD}
+    peak, peak_src = measured_peaks()
+    fpeak, mhz = fp32_peak_tflops(sms)
+
+    def render_roof(kname, n, ms):
+        k = kind_of[kname]
+        avg_ms = ms / max(1, n)
+        bytes_per_launch = float(np.mean(alg_bytes[k]))
+        flop = float(np.mean(n_eval[k])) * FLOP_PER_SAMPLE
+        achieved = flop / (avg_ms / 1000.0) / 1e12
+        # the render kernels are bound by instruction issue, not DRAM: their
+        # roof is FP32 throughput on the sample arithmetic
+        return {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": achieved / fpeak, "traffic": ncu_traffic(kname, name),
+                "kernel": kname, "avg_launch_ms": avg_ms,
+                "algorithmic_flop_per_launch": flop, "flop_per_sample": FLOP_PER_SAMPLE,
+                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz"
+                               % (sms, FP32_LANES_PER_SM, mhz),
+                "hbm": {"achieved_gbs": bytes_per_launch / (avg_ms / 1000.0) / 1e9,
+                        "peak_gbs": peak, "peak_source": peak_src,
+                        "algorithmic_bytes_per_launch": bytes_per_launch,
+                        "frac": bytes_per_launch / (avg_ms / 1000.0) / 1e9 / peak}}
+
+    renders = [(k, v) for k, v in prof.items() if k in kind_of]
+    dom_name, (dom_n, dom_ms) = max(renders, key=lambda kv: kv[1][1])
+    roof = render_roof(dom_name, dom_n, dom_ms)
+
+    # HBM roofline of every kernel with a fixed algorithmic byte count
+    gxyz = [(n + B - 1) // B for n in vshape]
+    n_bricks = int(np.prod(gxyz))
+    fixed_bytes = {"brick_minmax": nvox * itemsize + 8 * n_bricks, "brick_mask": 9 * n_bricks}
+    kroof = {}
+    for kname, (n, ms) in prof.items():
+        if kname in kind_of:
+            kroof[kname] = render_roof(kname, n, ms)
+            continue
+        if kname not in fixed_bytes:
+            continue
+        b = fixed_bytes[kname]
+        avg = ms / max(1, n)
+        ach = b / (avg / 1000.0) / 1e9
+        kroof[kname] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 5),
+                        "launches": n, "algorithmic_bytes_per_launch": b,
+                        "traffic": ncu_traffic(kname, name)}
+
+    per_frame = {ess.KIND_NAMES[kind_of[kname]]: ms / max(1, n)
+                 for kname, (n, ms) in prof.items() if kname in kind_of}
+    build_kernels = {nm: v for nm, v in prof.items() if not nm.startswith("render")}
+    edits = steps * len(tfs_np)
+    build_ms = {
+        "all_structures_per_edit": sum(v[1] for v in build_kernels.values()) / edits,
+        "note": "event intervals of the build kernels on the library's build stream, which run "
+                "while the frames of the same edit render",
+        "alone_per_edit": sum(v[1] for v in prof_alone.values()) / edits,
+        "alone_by_kernel": {nm: round(v[1] / edits, 4) for nm, v in prof_alone.items()},
+        "brick_minmax_launches_per_edit": prof.get("brick_minmax", (0, 0.0))[0] / edits}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
+        "steps": steps, "warmup": warmup, "ms_per_step": t_ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": name + ": " + w["desc"],
+                   "structures": [ess.KIND_NAMES[k] for k in kinds],
+                   "kd": KD_PARAMS, "brick": B, "image": "%dx%d" % (W, H),
+                   "tf_edits_per_step": len(tfs_np), "frames_per_step": frames_step,
+                   "nonempty_brick_fraction": [round(x, 4) for x in nonempty],
+                   "l2": "flushed between timed steps (%d MiB write, untimed)" % (L2_FLUSH_BYTES >> 20),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "evaluated_samples_per_s": job_rate(evaluated_step, ws, steps, t_ms),
+        "evaluated_samples_per_s_note": "ray samples/s as evaluated samples / time: the samples the "
+                                        "skipping renderers actually take",
+        "samples_per_frame": {"naive_equivalent": float(np.mean(n_naive)),
+                              **{ess.KIND_NAMES[k]: float(np.mean(v)) for k, v in n_eval.items()}},
+        "ms_per_frame": per_frame,
+        "naive_ms_per_frame": float(np.mean(naive_ms)),
+        "build_ms_per_edit": build_ms,
+        "kernel_ms": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_rooflines": kroof,
+        "clocks": clk,
+    }
+    if e2e_ms is not None:
+        result["e2e"] = {"value": job_rate(units_step, ws, steps, e2e_ms), "unit": "samples/s",
+                         "h2d_bytes_per_step": int(sum(t.numel() * 4 for t in tf_host)),
+                         "d2h_bytes_per_step": int(frames_step * W * H * 16),
+                         "ms_per_step": e2e_ms / steps}
+    env = dict(vol=vol, tf=tf, tf_dev=tf_dev, ecams=[vs[0] for vs in ecams], rp=rp, W=W, H=H,
+               B=B, structures=list(st.values()) + [naive], nvox=nvox, itemsize=itemsize,
+               tfs_np=tfs_np, views=views, vlo=vlo, vhi=vhi, vol_in=vol_in)
+    return result, env
+
+
+def release_env(ess, ctx, env):
+    for h in env["structures"]:
+        ess.ess_release(ctx, h)
+    ess.ess_release(ctx, env["tf"])
+    ess.ess_release(ctx, env["vol"])
+
+
+def run_fractal_leg(ess, torch, dev, stream, ctx, cpu, ref_budget, steps=2, warmup=1):
+    """The 1024^3 float32 field with a 1024-entry TF at 1920x1080 over 16 orbit
+    views (the paper compares the structures' build and render times per data
+    set, Table 2): per structure its rebuild (with the min/max pass over the
+    4 GiB volume) and its frames, each against its roofline, and the CPU
+    oracle on a row stripe of one view."""
+    res, env = measure_step(ess, torch, dev, stream, ctx, "fractal1024", steps, warmup,
+                            e2e=False, sample_clocks=False)
+    kr = res["kernel_rooflines"]
+    out = {"workload": res["config"]["workload"], "steps": steps,
+           "ms_per_step": res["ms_per_step"], "naive_equivalent_samples_per_s": res["value"],
+           "evaluated_samples_per_s": res["evaluated_samples_per_s"],
+           "nonempty_brick_fraction": res["config"]["nonempty_brick_fraction"],
+           "samples_per_frame": res["samples_per_frame"],
+           "naive_ms_per_frame": res["naive_ms_per_frame"],
+           "ms_per_frame": res["ms_per_frame"], "build_ms_per_edit": res["build_ms_per_edit"],
+           "render_rooflines": {k: v for k, v in kr.items() if k.startswith("render")},
+           "brick_minmax_roofline": kr.get("brick_minmax"), "gpu_launches": res["gpu_launches"]}
+    if cpu:
+        w = WORKLOADS["fractal1024"]
+        host = host_array(env["vol_in"])
+        cores = cpu_cores()
+        rate, desc = oracle_rate(host, 0.0, 1.0, env["tfs_np"][0], env["views"][0][0], w,
+                                 ref_budget, cores)
+        out["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": cores,
+                               "kind": "oracle", "sample": desc}
+        del host
+    release_env(ess, ctx, env)
+    del env
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, local, ws, dist):
     import torch
     import __graft_entry__
@@ -858,249 +1192,62 @@ def run_ours(args, rank, local, ws, dist):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = WORKLOADS[args.workload]
-    vol_np, (vlo, vhi), tfs_np, cams = make_inputs(args.workload)
-    W, H, B = w["W"], w["H"], w["brick"]
     stream = torch.cuda.Stream(device=dev)
-    kinds = [k for k in ess.KINDS if k != ess.NONE]
-
     with torch.cuda.stream(stream):
         ctx = ess.ess_create(local, stream)
-        vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).to(dev), vlo, vhi)
-        tf_dev = [torch.from_numpy(t).to(dev) for t in tfs_np]
-        tf_host = [torch.from_numpy(t).pin_memory() for t in tfs_np]
-        tf = ess.ess_tf_set(ctx, tf_dev[0])
-        # rescan: every rebuild recomputes the brick min/max from the voxels
-        params = {k: ess.build_params(brick=B, rescan=1, **KD_PARAMS) for k in kinds}
-        st = {k: ess.ess_build(ctx, vol, tf, k, params[k]) for k in kinds}
-        naive = ess.ess_build(ctx, vol, tf, ess.NONE)
-        outs = {k: torch.empty((H, W, 4), dtype=torch.float32, device=dev) for k in kinds}
-        host_out = torch.empty((H, W, 4), dtype=torch.float32).pin_memory()
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        rp = ess.render_params(w["dt"], w["ert"])
-        ecams = [ess.camera_from(c) for c in cams]
-
-        # per-edit reference counts (untimed): naive samples, evaluated samples,
-        # non-empty bricks, algorithmic bytes of each render
-        n_naive, n_eval, alg_bytes, nonempty = [], {k: [] for k in kinds}, {k: [] for k in kinds}, []
-        for i in range(len(tfs_np)):
-            ess.ess_tf_update(ctx, tf, tf_dev[i])
-            ess.ess_rebuild(ctx, naive)
-            ess.ess_sample_count(ctx, reset=True)
-            ess.ess_render(ctx, naive, ecams[i], rp, W, H, outs[kinds[0]])
-            n_naive.append(ess.ess_sample_count(ctx, reset=True))
-            for k in kinds:
-                ess.ess_rebuild(ctx, st[k])
-                ess.ess_render(ctx, st[k], ecams[i], rp, W, H, outs[k])
-                n_eval[k].append(ess.ess_sample_count(ctx, reset=True))
-                info = ess.ess_structure_info_get(ctx, st[k])
-                nb = info["n_nonempty"]
-                if k == kinds[0]:
-                    nonempty.append(nb / max(1, info["n_bricks"]))
-                # compulsory bytes of one frame: the image, the voxels of the
-                # non-empty bricks and the structure itself
-                struct_b = info["n_bricks"] if k == ess.GRID else 32 * max(1, info["n_nodes"])
-                alg_bytes[k].append(W * H * 16 + nb * B ** 3 * vol_np.itemsize + struct_b)
-        ess.ess_sync(ctx)
-
-        def step(host_io=False):
-            # the library runs the rebuilds on its build stream: the k-d and LBVH
-            # rebuilds overlap the grid's frame
-            for i in range(len(tfs_np)):
-                ess.ess_tf_update(ctx, tf, tf_host[i] if host_io else tf_dev[i])
-                for k in kinds:
-                    ess.ess_rebuild(ctx, st[k])
-                for k in kinds:
-                    ess.ess_render(ctx, st[k], ecams[i], rp, W, H, host_out if host_io else outs[k])
-
-        for _ in range(args.warmup):
-            step()
-        ess.ess_sync(ctx)
-        launches0 = ess.ess_launch_count(ctx)
-        ess.ess_profile_reset(ctx)
-        ess.ess_profile_enable(ctx, True)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        clocks = ClockSampler(local)
-        for s in range(args.steps):
-            flush.zero_()                        # L2 flush between timed steps (untimed)
-            ev[s][0].record(stream)
-            step()
-            ev[s][1].record(stream)
-        torch.cuda.synchronize(dev)
-        clk = clocks.stop()
-        launches = ess.ess_launch_count(ctx) - launches0
-        ess.ess_profile_enable(ctx, False)
-        prof = ess.ess_profile_read(ctx)
-        ess.ess_sync(ctx)
-        t_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev), dev)
-
-        # end to end through the ABI with host buffers
-        for _ in range(max(1, args.warmup // 2)):
-            step(host_io=True)
-        ess.ess_sync(ctx)
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            step(host_io=True)
-        ess.ess_sync(ctx)
-        e2e_ms = max_over_ranks(dist, 1000.0 * (time.perf_counter() - t0), dev)
-
-        # the step's rebuilds alone (no frame beside them): per edit, the TF
-        # upload and the three rebuilds, waited for before the next edit
-        ess.ess_profile_reset(ctx)
-        ess.ess_profile_enable(ctx, True)
-        for _ in range(args.steps):
-            for i in range(len(tfs_np)):
-                ess.ess_tf_update(ctx, tf, tf_dev[i])
-                for k in kinds:
-                    ess.ess_rebuild(ctx, st[k])
-                ess.ess_sync(ctx)
-        ess.ess_profile_enable(ctx, False)
-        prof_alone = ess.ess_profile_read(ctx)
-
-    units_step = sum(n_naive) * len(kinds)
-    evaluated_step = sum(sum(v) for v in n_eval.values())
-    value = job_rate(units_step, ws, args.steps, t_ms)
-    e2e_value = job_rate(units_step, ws, args.steps, e2e_ms)
-
-    # dominant kernel and its roofline on algorithmic bytes (among the renders:
-    # the build kernels run on the build stream alongside them, so their event
-    # intervals include the time they share the GPU with a render)
-    kind_of = {"render_grid": ess.GRID, "render_lbvh": ess.LBVH, "render_kd": ess.KD}
-    dom = max(((k, v) for k, v in prof.items() if k in kind_of), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms) = dom
-    avg_ms = dom_ms / max(1, dom_launches)
-    peak, peak_src = measured_peaks()
-    if dom_name in kind_of and kind_of[dom_name] in alg_bytes:
-        bytes_per_launch = float(np.mean(alg_bytes[kind_of[dom_name]]))
-    else:
-        bytes_per_launch = None
-    roof = None
-    if dom_name in kind_of and kind_of[dom_name] in n_eval:
-        # the render kernels are bound by instruction issue, not DRAM: their
-        # roof is FP32 throughput on the sample arithmetic
-        flop = float(np.mean(n_eval[kind_of[dom_name]])) * FLOP_PER_SAMPLE
-        achieved = flop / (avg_ms / 1000.0) / 1e12
-        fpeak, mhz = fp32_peak_tflops()
-        roof = {"bound": "alu", "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
-                "frac": achieved / fpeak, "traffic": ncu_traffic(dom_name, args.workload),
-                "kernel": dom_name, "avg_launch_ms": avg_ms,
-                "algorithmic_flop_per_launch": flop, "flop_per_sample": FLOP_PER_SAMPLE,
-                "peak_source": "derived: %d SMs x %d FP32 lanes x 2 FLOP x %.0f MHz"
-                               % (SMS, FP32_LANES_PER_SM, mhz),
-                "hbm": {"achieved_gbs": bytes_per_launch / (avg_ms / 1000.0) / 1e9,
-                        "peak_gbs": peak, "peak_source": peak_src,
-                        "algorithmic_bytes_per_launch": bytes_per_launch}}
-    elif bytes_per_launch is not None:
-        achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(dom_name, args.workload),
-                "kernel": dom_name, "avg_launch_ms": avg_ms,
-                "algorithmic_bytes_per_launch": bytes_per_launch, "peak_source": peak_src}
-
-    # HBM roofline of every kernel with a fixed algorithmic byte count
-    nvox = int(np.prod(vol_np.shape))
-    gxyz = [(n + B - 1) // B for n in vol_np.shape]
-    n_bricks = int(np.prod(gxyz))
-    fixed_bytes = {"brick_minmax": nvox * vol_np.itemsize + 8 * n_bricks,
-                   "brick_mask": 9 * n_bricks}
-    kroof = {}
-    for name, (n, ms) in prof.items():
-        if name in fixed_bytes:
-            b = fixed_bytes[name]
-        elif name in kind_of and kind_of[name] in alg_bytes:
-            b = float(np.mean(alg_bytes[kind_of[name]]))
-        else:
-            continue
-        avg = ms / max(1, n)
-        ach = b / (avg / 1000.0) / 1e9
-        kroof[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                       "frac": round(ach / peak, 4), "avg_launch_ms": round(avg, 5),
-                       "algorithmic_bytes_per_launch": b,
-                       "traffic": ncu_traffic(name, args.workload)}
-
-    per_frame = {}
-    build_ms = {}
-    for name, (n, ms) in prof.items():
-        for kname, k in kind_of.items():
-            if name == kname:
-                per_frame[ess.KIND_NAMES[k]] = ms / max(1, n)
-    build_kernels = {nm: v for nm, v in prof.items() if not nm.startswith("render")}
-    total_build_ms = sum(v[1] for v in build_kernels.values())
-    edits = args.steps * len(tfs_np)
-    build_ms["all_structures_per_edit"] = total_build_ms / edits
-    build_ms["note"] = ("event intervals of the build kernels on the library's build stream, which "
-                        "run while the frames of the same edit render")
-    build_ms["alone_per_edit"] = sum(v[1] for v in prof_alone.values()) / edits
-    build_ms["alone_by_kernel"] = {nm: round(v[1] / edits, 4) for nm, v in prof_alone.items()}
-
-    result = {
-        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": args.workload + ": " + w["desc"],
-                   "structures": [ess.KIND_NAMES[k] for k in kinds],
-                   "kd": KD_PARAMS, "brick": B, "image": "%dx%d" % (W, H),
-                   "tf_edits_per_step": len(tfs_np),
-                   "nonempty_brick_fraction": [round(x, 4) for x in nonempty],
-                   "l2": "flushed between timed steps (%d MiB write, untimed)" % (L2_FLUSH_BYTES >> 20),
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "evaluated_samples_per_s": job_rate(evaluated_step, ws, args.steps, t_ms),
-        "samples_per_frame": {"naive_equivalent": float(np.mean(n_naive)),
-                              **{ess.KIND_NAMES[k]: float(np.mean(v)) for k, v in n_eval.items()}},
-        "ms_per_frame": per_frame,
-        "build_ms_per_edit": build_ms,
-        "kernel_ms": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
-        "gpu_launches": int(launches),
-        "roofline": roof,
-        "kernel_rooflines": kroof,
-        "paper_context": {
+        result, env = measure_step(ess, torch, dev, stream, ctx, args.workload, args.steps,
+                                   args.warmup, dist=dist, ws=ws)
+    if args.workload == "ct512":
+        result["paper_context"] = {
             "source": "Table 2 of the paper (NVIDIA Titan V, Xeon Gold 5122; Sec. 4.1)",
             "note": "real 512^3-class data sets, 1024^2 orthographic, early termination and "
                     "shading off: context, not a target; this run's frames/s are 1000 / "
                     "ms_per_frame and its builds are in build_ms_per_edit and structures",
             "rows": PAPER_TABLE2_512,
-            "this_run_fps": {k: round(1000.0 / v, 1) for k, v in per_frame.items()}},
-        "e2e": {"value": e2e_value, "unit": "samples/s",
-                "h2d_bytes_per_step": int(sum(t.numel() * 4 for t in tf_host)),
-                "d2h_bytes_per_step": int(len(tfs_np) * len(kinds) * W * H * 16),
-                "ms_per_step": e2e_ms / args.steps},
-        "clocks": clk,
-    }
-    if not args.no_hybrid:
+            "this_run_fps": {k: round(1000.0 / v, 1) for k, v in result["ms_per_frame"].items()}}
+    vol, tf, tf_dev, ecams = env["vol"], env["tf"], env["tf_dev"], env["ecams"]
+    rp, W, H, B = env["rp"], env["W"], env["H"], env["B"]
+    ct = args.workload == "ct512"   # the legs below run on the 512^3 workload's TF edits
+    if ct and not args.no_hybrid:
         with torch.cuda.stream(stream):
             result["hybrid"] = run_hybrid(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp, W, H)
-    if not args.no_cell_vote:
+    if ct and not args.no_cell_vote:
         with torch.cuda.stream(stream):
             result["cell_vote"] = run_cell_vote(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, rp,
-                                                W, H, B, vol_np.nbytes)
-    if not args.no_shaded:
+                                                W, H, B, env["nvox"] * env["itemsize"])
+    if ct and not args.no_shaded:
         with torch.cuda.stream(stream):
             result["shaded"] = run_shaded(ess, torch, dev, ctx, vol, tf, tf_dev, ecams, W, H, B,
                                           KD_PARAMS)
-    if not args.no_structures:
+    if ct and not args.no_structures:
         with torch.cuda.stream(stream):
             result["structures"] = run_structures(ess, torch, dev, ctx, vol, tf, tf_dev, ecams,
                                                   rp, W, H)
+    vol_host = host_array(env["vol_in"])
+    vlo, vhi, tfs_np, views = env["vlo"], env["vhi"], env["tfs_np"], env["views"]
+    with torch.cuda.stream(stream):
+        release_env(ess, ctx, env)
+    del env
+    torch.cuda.empty_cache()
+    if ct and not args.no_fractal:
+        with torch.cuda.stream(stream):
+            result["fractal1024"] = run_fractal_leg(
+                ess, torch, dev, stream, ctx, rank == 0 and ws == 1 and not args.no_cpu_baseline,
+                min(args.ref_budget, 4.0))
     if not args.no_batched:
         with torch.cuda.stream(stream):
             result["batched"] = run_batched(ess, torch, dev, stream, ctx)
-    if not args.no_serve:
+    if ct and not args.no_serve:
         with torch.cuda.stream(stream):
-            result["served"] = run_served(ess, torch, dev, ctx, vol_np)
+            result["served"] = run_served(ess, torch, dev, ctx, vol_host)
     if not args.no_minmax:
         with torch.cuda.stream(stream):
             result["minmax_sweep"] = run_minmax_sweep(ess, torch, dev, ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
-        rate, desc = oracle_rate(vol_np, vlo, vhi, tfs_np[0], cams[0], w, args.ref_budget, cores)
+        w = WORKLOADS[args.workload]
+        rate, desc = oracle_rate(vol_host, vlo, vhi, tfs_np[0], views[0][0], w, args.ref_budget,
+                                 cores)
         result["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": cores,
                                   "kind": "oracle", "sample": desc}
     with torch.cuda.stream(stream):
@@ -1133,6 +1280,8 @@ def make_parser():
                     help="skip the shaded-render workload (gradient shading, opacity correction)")
     ap.add_argument("--no-structures", action="store_true",
                     help="skip the structure comparison (node counts, heights, build and frame times)")
+    ap.add_argument("--no-fractal", action="store_true",
+                    help="skip the 1024^3 float32 leg (16 views at 1920x1080, every structure)")
     return ap
 
 

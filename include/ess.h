@@ -112,7 +112,9 @@ ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
  * cells of the 8 clamped voxels one trilinear sample interpolates (8x the
  * volume's bytes; one vector load per sample); cells = 0 drops that copy and
  * reads the 8 voxels from the volume itself.  ess_volume_upload keeps the copy
- * when it fits in half of the free device memory. */
+ * when it fits in half of the free device memory and has fewer than 2^32 cells
+ * (about 1625^3 voxels; the renderer indexes cells with 32-bit integers);
+ * ESS_ERR_ARG for cells = 1 on a larger volume. */
 ess_status ess_volume_set_sampler(ess_ctx *ctx, ess_handle vol, int cells);
 
 /* Sets an RGBA transfer function of `nt` entries (Sec. 1: the colour and
@@ -144,13 +146,20 @@ typedef struct {
     int mls;     /* k-d maximum leaf size (Sec. 4.3) as an edge in voxels
                     (32 or 128 in the paper), 0 = none */
     int empty_test; /* 0 = brick min/max range test (Sec. 2, min-max range
-                    queries), 1 = per-cell vote (Sec. 3.1 classifies per voxel) */
-    int rescan;  /* empty_test 0 only: 1 = recompute the per-brick min/max
-                    from the voxels in every build and rebuild (a full pass
-                    over the volume per TF edit, as when bricks are classified
-                    from their voxels after each edit, Sec. 3.1); 0 = compute
-                    it once per volume and brick size and reuse it (it does
-                    not depend on the TF).  Both give the same mask. */
+                    queries), 1 = exact per-cell vote (Sec. 3.1 classifies per
+                    voxel): a brick is non-empty iff one of the trilinear
+                    cells whose samples touch it passes the range test of its
+                    8 corner voxels; evaluated on the bricks the min/max test
+                    passes (it never marks another) */
+    int rescan;  /* 1 = recompute the per-brick min/max
+                    from the voxels once per TF edit (a full pass over the
+                    volume per edit, as when bricks are classified from their
+                    voxels after each edit, Sec. 3.1): the first build or
+                    rebuild of a (volume, brick size) after any TF upload of
+                    the context reads the volume, and the structures rebuilt
+                    after it for the same edit reuse that pass; 0 = compute it
+                    once per volume and brick size and reuse it (it does not
+                    depend on the TF).  Both give the same mask. */
 } ess_build_params;
 
 /* Builds a skipping structure of `kind` for volume `vol` under TF `tf`
@@ -171,8 +180,9 @@ ess_status ess_rebuild(ess_ctx *ctx, ess_handle structure);
 /* Rebuilds `count` distinct structures (1 <= count <= 4096), e.g. one per TF
  * of a batch of many TFs over one volume, with the same results as calling
  * ess_rebuild on each.  Together: the per-brick min/max of structures built
- * with rescan = 1 is recomputed once per (volume, brick size) of the batch,
- * not once per structure, and the structures' build chains run on several
+ * with rescan = 1 is recomputed once per (volume, brick size) of the batch
+ * (and not at all where this TF edit's pass already ran), not once per
+ * structure, and the structures' build chains run on several
  * internal streams at once, so that their latency-bound kernels overlap.
  * Asynchronous; later users of each structure wait for its build as usual.
  * ESS_ERR_ARG for a repeated handle, ESS_ERR_HANDLE for a bad one. */
@@ -224,7 +234,7 @@ typedef struct {
     float v[3];    /* up, scaled: perspective tan(fov/2), ortho half height */
     float w[3];    /* forward (normalised before use) */
     int ortho;     /* 1 = orthographic (Sec. 4.1), 0 = perspective */
-} ess_camera;
+} ess_camera;   /* finite; |eye[i]| + |u[i]| + |v[i]| <= 65536 voxels per axis */
 
 typedef struct {
     float dt;     /* step between samples in voxels, 1e-3 <= dt <= 1e4 */

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ess_internal.h"
 
 namespace ess {
@@ -557,6 +559,11 @@ bool launch_minmax_vec(Ctx &c, const T *data, int nx, int ny, int nz, int B, int
 void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out)
 {
     int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
+    // rows of whole 16-byte blocks and bricks up to 8^3: staged by the tensor
+    // copy engine (minmax_tma.cu); measured on a GB300 it moves 8^3-brick
+    // tiles faster than the cp.async pipeline below, which is faster for the
+    // larger bricks (their tiles hold more rows per thread)
+    if (B <= 8 && launch_brick_minmax_tma(c, v, B, out)) return;
     bool done = false;
     switch (v.dtype) {
     case ESS_U8:
@@ -594,9 +601,18 @@ void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out)
 // [0, 1] sets DEV_ERR_BAD_TF (tables uploaded from device memory are checked
 // here so that a TF edit never waits for the host).
 __global__ void __launch_bounds__(1024) k_tf_prefix(const float4 *__restrict__ table, int nt,
-                                                    int *__restrict__ prefix, int validate,
+                                                    int *__restrict__ prefix,
+                                                    float4 *__restrict__ lut, int validate,
                                                     uint32_t *status)
 {
+    // the renderer's interpolation table: entry i and the difference to entry
+    // i + 1 (the table's entry nt repeats nt - 1), rounded to float32 exactly
+    // as the lerp fmaf(w, c1 - c0, c0) of R5 rounds it
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const float4 c0 = table[i], c1 = table[i + 1];
+        lut[2 * i] = c0;
+        lut[2 * i + 1] = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
+    }
     __shared__ int warp_tot[32];
     int t = threadIdx.x;
     int per = (nt + 1023) / 1024;
@@ -635,10 +651,11 @@ __global__ void __launch_bounds__(1024) k_tf_prefix(const float4 *__restrict__ t
     if (t == 1023) prefix[nt] = warp_tot[31];
 }
 
-void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, int validate)
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, float4 *lut,
+                      int validate)
 {
     Launch L(c, "tf_prefix");
-    k_tf_prefix<<<1, 1024, 0, c.stream>>>(table, nt, prefix, validate, c.dev_status);
+    k_tf_prefix<<<1, 1024, 0, c.stream>>>(table, nt, prefix, lut, validate, c.dev_status);
 }
 
 // ---------------------------------------------------- K2 range test (mask)
@@ -670,95 +687,89 @@ void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf, f
 
 // ------------------------------------------------ per-cell vote variant
 // The paper's LBVH classifier decides visibility per voxel and lets the
-// threads of a brick vote through a shared-memory flag (Sec. 3.1).  The
-// conservative form of that vote for interpolated samples: one thread per
-// trilinear cell c (corner voxels c..c+1, clamped; c in [-1, n-1]) tests the
-// range of its 8 corner values; a positive cell marks every brick whose closed
-// region its sample region [c+0.5, c+1.5) touches, with an idempotent store
-// of 1.  A block covers an 8x8x4 tile of cells and leaves early when none of
-// its cells is positive.
+// threads of a brick vote (Sec. 3.1).  The exact form of that vote for
+// interpolated samples: brick b is non-empty iff some trilinear cell c whose
+// sample region [c+0.5, c+1.5) touches the brick's closed region (per axis
+// c = bB-1 .. min((b+1)B, n)-1, corner voxels c and c+1 clamped) passes the
+// range test of its own 8 corner values.  Those corners all lie in the
+// brick's apron, so a cell's range lies inside the brick's min/max range and
+// the vote can only clear bricks that the range test marked: the mask is
+// first the range test's (K2, from the min/max of the volume pass K1), then
+// one warp per marked brick tests its cells 32 at a time and stops at the
+// first positive one; a brick without one is cleared.  Bricks the range test
+// passes are nearly always truly visible, so the typical brick costs one
+// round of 32 cells.
 template <typename T>
-__global__ void __launch_bounds__(256) k_mask_cells(const T *__restrict__ vol, int nx, int ny,
-                                                    int nz, int B, int gx, int gy, int gz,
-                                                    const int *__restrict__ prefix, int nt,
-                                                    float value_lo, float s,
-                                                    uint8_t *__restrict__ mask)
+__global__ void __launch_bounds__(256) k_vote_bricks(const T *__restrict__ vol, int nx, int ny,
+                                                     int nz, int B, int gx, int gy, int64_t nb,
+                                                     const int *__restrict__ prefix, int nt,
+                                                     float value_lo, float s,
+                                                     uint8_t *__restrict__ mask)
 {
-    // tile origin in cell coordinates (cells start at -1)
-    int cx = blockIdx.x * 8 + (threadIdx.x & 7) - 1;
-    int cy = blockIdx.y * 8 + ((threadIdx.x >> 3) & 7) - 1;
-    int cz = blockIdx.z * 4 + (threadIdx.x >> 6) - 1;
-    bool pos = false;
-    if (cx < nx && cy < ny && cz < nz) {
-        int x0 = max(cx, 0), x1 = min(cx + 1, nx - 1);
-        int y0 = max(cy, 0), y1 = min(cy + 1, ny - 1);
-        int z0 = max(cz, 0), z1 = min(cz + 1, nz - 1);
-        float mn = INFINITY, mx = -INFINITY;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float xmax = (float)(nt - 1);
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
+        if (mask[b] == 0) continue;  // uniform: the range test already cleared it
+        const int bx = (int)(b % gx), by = (int)((b / gx) % gy), bz = (int)(b / ((int64_t)gx * gy));
+        // cells touching the brick, per axis: lo .. hi (lo >= -1, hi <= n - 1)
+        const int lx = bx * B - 1, ly = by * B - 1, lz = bz * B - 1;
+        const int ex = min((bx + 1) * B, nx) - 1 - lx + 1;
+        const int ey = min((by + 1) * B, ny) - 1 - ly + 1;
+        const int ez = min((bz + 1) * B, nz) - 1 - lz + 1;
+        const int ncell = ex * ey * ez;
+        bool found = false;
+        for (int base = 0; base < ncell && !found; base += 32) {  // uniform
+            const int i = base + lane;
+            bool pos = false;
+            if (i < ncell) {
+                const int cx = lx + i % ex, cy = ly + (i / ex) % ey, cz = lz + i / (ex * ey);
+                const int x0 = max(cx, 0), x1 = min(cx + 1, nx - 1);
+                const int y0 = max(cy, 0), y1 = min(cy + 1, ny - 1);
+                const int z0 = max(cz, 0), z1 = min(cz + 1, nz - 1);
+                float mn = INFINITY, mx = -INFINITY;
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    size_t idx = ((size_t)(dz ? z1 : z0) * ny + (dy ? y1 : y0)) * (size_t)nx +
-                                 (dx ? x1 : x0);
-                    float v = to_f(__ldg(vol + idx));
+                for (int k = 0; k < 8; ++k) {
+                    const size_t idx = ((size_t)((k & 4) ? z1 : z0) * ny + ((k & 2) ? y1 : y0)) *
+                                           (size_t)nx + ((k & 1) ? x1 : x0);
+                    const float v = to_f(__ldg(vol + idx));
                     mn = v < mn ? v : mn;
                     mx = v > mx ? v : mx;
                 }
-        float xmax = (float)(nt - 1);
-        int lo = (int)tf_coord(mn, value_lo, s, xmax);
-        int hi = (int)tf_coord(mx, value_lo, s, xmax) + 1;
-        hi = hi > nt - 1 ? nt - 1 : hi;
-        pos = (__ldg(prefix + hi + 1) - __ldg(prefix + lo)) > 0;
-    }
-    if (!__syncthreads_or(pos)) return;
-    if (!pos) return;
-    // bricks b with 2c+1 <= 2*min((b+1)B, n) and 2c+3 >= 2bB, per axis; as
-    // c <= n-1 the clamp at n never decides the first condition
-    int c[3] = {cx, cy, cz}, g[3] = {gx, gy, gz};
-    int blo[3], bhi[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        // lowest b: need (b+1)B >= c + 0.5 (or the clamp at n): b >= ceil((c+0.5)/B) - 1
-        int lo = (2 * c[a] + 1 + 2 * B - 1) / (2 * B) - 1;
-        if (2 * c[a] + 1 < 0) lo = 0;
-        lo = max(lo, 0);
-        // highest b: need bB <= c + 1.5: b <= floor((2c+3)/(2B))
-        int hi = (2 * c[a] + 3) / (2 * B);
-        hi = min(hi, g[a] - 1);
-        blo[a] = lo;
-        bhi[a] = hi;
-    }
-    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
-        for (int by = blo[1]; by <= bhi[1]; ++by)
-            for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
-                uint8_t *f = mask + ((size_t)bz * gy + by) * gx + bx;
-                if (*(volatile uint8_t *)f == 0) *f = 1;
+                const int lo = (int)tf_coord(mn, value_lo, s, xmax);
+                int hi = (int)tf_coord(mx, value_lo, s, xmax) + 1;
+                hi = hi > nt - 1 ? nt - 1 : hi;
+                pos = (__ldg(prefix + hi + 1) - __ldg(prefix + lo)) > 0;
             }
+            found = __any_sync(0xffffffffu, pos);
+        }
+        if (!found && lane == 0) mask[b] = 0;
+    }
 }
 
-void launch_brick_mask_cells(Ctx &c, const Volume &v, int B, const TF &tf, float s, uint8_t *mask,
-                             int gx, int gy, int gz)
+void launch_vote_bricks(Ctx &c, const Volume &v, int B, const TF &tf, float s, uint8_t *mask,
+                        int gx, int gy, int gz)
 {
-    ESS_CUDA(cudaMemsetAsync(mask, 0, (size_t)gx * gy * gz, c.stream));
-    dim3 grid((v.nx + 1 + 7) / 8, (v.ny + 1 + 7) / 8, (v.nz + 1 + 3) / 4);
-    Launch L(c, "mask_cells");
+    int sms = 0;
+    ESS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    const int64_t nb = (int64_t)gx * gy * gz;
+    const int blocks = (int)std::min<int64_t>((int64_t)sms * 8, (nb + 7) / 8);
+    Launch L(c, "vote_bricks");
     switch (v.dtype) {
     case ESS_U8:
-        k_mask_cells<uint8_t><<<grid, 256, 0, c.stream>>>((const uint8_t *)v.data, v.nx, v.ny, v.nz,
-                                                          B, gx, gy, gz, tf.prefix, tf.nt,
-                                                          v.value_lo, s, mask);
+        k_vote_bricks<uint8_t><<<blocks, 256, 0, c.stream>>>((const uint8_t *)v.data, v.nx, v.ny,
+                                                             v.nz, B, gx, gy, nb, tf.prefix,
+                                                             tf.nt, v.value_lo, s, mask);
         break;
     case ESS_U16:
-        k_mask_cells<uint16_t><<<grid, 256, 0, c.stream>>>((const uint16_t *)v.data, v.nx, v.ny,
-                                                           v.nz, B, gx, gy, gz, tf.prefix, tf.nt,
-                                                           v.value_lo, s, mask);
+        k_vote_bricks<uint16_t><<<blocks, 256, 0, c.stream>>>((const uint16_t *)v.data, v.nx, v.ny,
+                                                              v.nz, B, gx, gy, nb, tf.prefix,
+                                                              tf.nt, v.value_lo, s, mask);
         break;
     default:
-        k_mask_cells<float><<<grid, 256, 0, c.stream>>>((const float *)v.data, v.nx, v.ny, v.nz, B,
-                                                        gx, gy, gz, tf.prefix, tf.nt, v.value_lo,
-                                                        s, mask);
+        k_vote_bricks<float><<<blocks, 256, 0, c.stream>>>((const float *)v.data, v.nx, v.ny, v.nz,
+                                                           B, gx, gy, nb, tf.prefix, tf.nt,
+                                                           v.value_lo, s, mask);
     }
 }
 

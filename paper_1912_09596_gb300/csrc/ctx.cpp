@@ -214,15 +214,24 @@ void load_tf(Ctx &c, TF &t, const float *rgba, int on_device)
     // entry nt repeats entry nt-1 so that the renderer's upper neighbour needs no clamp
     ESS_CUDA(cudaMemcpyAsync(t.table + t.nt, t.table + (t.nt - 1), sizeof(float4),
                              cudaMemcpyDeviceToDevice, c.stream));
-    launch_tf_prefix(c, t.table, t.nt, t.prefix, on_device);
+    launch_tf_prefix(c, t.table, t.nt, t.prefix, t.lut, on_device);
     mark(c, t.updated);
     ++t.version;
+    ++c.edit_epoch;
 }
 
 // Builds (mode 1) or drops (mode 0) the corner-replicated cell copy.
+// The renderer indexes cells with 32-bit integers.
+bool cells_indexable(const Volume &v)
+{
+    return (uint64_t)(v.nx + 1) * (uint64_t)(v.ny + 1) * (uint64_t)(v.nz + 1) <= 0xffffffffull;
+}
+
 void set_sampler(Ctx &c, Volume &v, int mode)
 {
     if (mode == 1) {
+        ESS_REQUIRE(cells_indexable(v),
+                    "the cell sampler needs (nx+1)(ny+1)(nz+1) < 2^32 (about 1625^3 voxels)");
         if (!v.cells) {
             v.cell_bytes = cell_array_bytes(v);
             v.cells = c.alloc(v.cell_bytes);
@@ -238,18 +247,25 @@ void set_sampler(Ctx &c, Volume &v, int mode)
 }
 
 // Per-brick min/max of volume v for brick size B, computed on first use and
-// kept with the volume; `rescan` recomputes a kept one.
+// kept with the volume.  `rescan` recomputes a kept one, as the paper's
+// classification reads the volume on every TF edit (Sec. 3.1), but only once
+// per edit: the structures rebuilt for the same edit share the pass (the
+// values are TF-independent, so any pass gives the same bits).
 float2 *minmax_for(Ctx &c, Volume &v, int B, bool rescan)
 {
     auto it = v.minmax.find(B);
     if (it != v.minmax.end()) {
-        if (rescan) launch_brick_minmax(c, v, B, it->second);
+        if (rescan && v.scan_epoch[B] != c.edit_epoch) {
+            launch_brick_minmax(c, v, B, it->second);
+            v.scan_epoch[B] = c.edit_epoch;
+        }
         return it->second;
     }
     int gx = (v.nx + B - 1) / B, gy = (v.ny + B - 1) / B, gz = (v.nz + B - 1) / B;
     float2 *mm = (float2 *)c.alloc(sizeof(float2) * (size_t)gx * gy * gz);
     launch_brick_minmax(c, v, B, mm);
     v.minmax[B] = mm;
+    v.scan_epoch[B] = c.edit_epoch;
     return mm;
 }
 
@@ -317,12 +333,10 @@ void run_build(Ctx &c, Structure &s)
     TF &t = get_tf(c, s.tf);
     int B = s.p.brick;
     float sc = (float)(t.nt - 1) / (v.value_hi - v.value_lo);
-    if (s.p.empty_test == 1) {
-        launch_brick_mask_cells(c, v, B, t, sc, s.mask, s.gx, s.gy, s.gz);
-    } else {
-        float2 *mm = minmax_for(c, v, B, s.p.rescan == 1);
-        launch_brick_mask(c, mm, s.nb, t, v.value_lo, sc, s.mask);
-    }
+    float2 *mm = minmax_for(c, v, B, s.p.rescan == 1);
+    launch_brick_mask(c, mm, s.nb, t, v.value_lo, sc, s.mask);
+    // the exact per-cell vote clears the range test's bricks that no cell shows
+    if (s.p.empty_test == 1) launch_vote_bricks(c, v, B, t, sc, s.mask, s.gx, s.gy, s.gz);
     launch_compact(c, s.mask, s.nb, s.ids, s.count, s.block_sums,
                    s.kind == ESS_LBVH ? s.keys : nullptr, s.gx, s.gy);
     s.n_host = -1;
@@ -387,6 +401,15 @@ void build_on(Ctx &c, Structure &s, cudaStream_t st)
 void run_build_async(Ctx &c, Structure &s, bool first)
 {
     ensure_build_stream(c);
+    if (c.batch_streams_pending) {
+        // builds of an ess_rebuild_batch may still read (or rescan) the
+        // volumes' min/max that this build reads or rescans
+        for (cudaStream_t st : c.batch_streams) {
+            ESS_CUDA(cudaEventRecord(c.fork_event, st));
+            ESS_CUDA(cudaStreamWaitEvent(c.build_stream, c.fork_event, 0));
+        }
+        c.batch_streams_pending = false;
+    }
     if (first) {
         ESS_CUDA(cudaEventRecord(c.fork_event, c.stream));
         ESS_CUDA(cudaStreamWaitEvent(c.build_stream, c.fork_event, 0));
@@ -425,6 +448,12 @@ void check_render_args(const ess_camera *camera, const ess_render_params *params
                     "camera must be finite");
     ESS_REQUIRE(camera->w[0] != 0.0f || camera->w[1] != 0.0f || camera->w[2] != 0.0f,
                 "camera needs a non-zero forward vector");
+    // ray origins within 2^16 voxels of the volume's corner keep the rounding
+    // of sample positions far below half a voxel (the renderer relies on it)
+    for (int i = 0; i < 3; ++i)
+        ESS_REQUIRE(std::fabs(camera->eye[i]) + std::fabs(camera->u[i]) + std::fabs(camera->v[i]) <=
+                        65536.0f,
+                    "camera eye +- u +- v must lie within 65536 voxels of the origin");
     ESS_REQUIRE(params->shading == 0 || params->shading == 1, "shading must be 0 or 1");
     if (params->shading) {
         ESS_REQUIRE(std::isfinite(params->ka) && std::isfinite(params->kd) &&
@@ -489,9 +518,11 @@ ess_status ess_destroy(ess_ctx *ctx)
         for (auto &kv : c.tfs) {
             c.free(kv.second->table);
             c.free(kv.second->prefix);
+            c.free(kv.second->lut);
         }
         c.free(c.stage);
         c.free(c.selftest_flag);
+        for (auto &kv : c.tile_counters) c.free(kv.second);
         ESS_CUDA(cudaStreamSynchronize(c.stream));
         for (auto &kv : c.tfs) {
             for (int k = 0; k < STAGE_RING; ++k) {
@@ -569,6 +600,7 @@ ess_status ess_release(ess_ctx *ctx, ess_handle h)
             if (t.refs > 0) throw Error{ESS_ERR_ARG, "TF still used by a structure"};
             c.free(t.table);
             c.free(t.prefix);
+            c.free(t.lut);
             ESS_CUDA(cudaStreamSynchronize(c.stream));
             for (int k = 0; k < STAGE_RING; ++k) {
                 if (t.staging[k]) cudaFreeHost(t.staging[k]);
@@ -623,7 +655,7 @@ ess_status ess_volume_upload(ess_ctx *ctx, const void *data, int data_on_device,
         // fit in half of the free device memory
         size_t free_b = 0, total_b = 0;
         ESS_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        if (cell_array_bytes(*v) < free_b / 2) set_sampler(c, *v, 1);
+        if (cells_indexable(*v) && cell_array_bytes(*v) < free_b / 2) set_sampler(c, *v, 1);
         ess_handle h = new_handle(c, TAG_VOL);
         c.volumes[h] = std::move(v);
         *vol = h;
@@ -650,11 +682,13 @@ ess_status ess_tf_set(ess_ctx *ctx, const float *rgba, int on_device, int nt, es
         t->nt = nt;
         t->table = (float4 *)c.alloc(sizeof(float4) * (nt + 1));
         t->prefix = (int *)c.alloc(sizeof(int) * (nt + 1));
+        t->lut = (float4 *)c.alloc(sizeof(float4) * 2 * (size_t)nt);
         try {
             load_tf(c, *t, rgba, on_device);
         } catch (...) {
             c.free(t->table);
             c.free(t->prefix);
+            c.free(t->lut);
             throw;
         }
         ess_handle h = new_handle(c, TAG_TF);
@@ -763,17 +797,25 @@ ess_status ess_rebuild_batch(ess_ctx *ctx, const ess_handle *structures, int cou
             ESS_CUDA(cudaEventCreateWithFlags(&c.rescan_event, cudaEventDisableTiming));
         }
         // one min/max rescan per (volume, brick size), on the first stream,
-        // after every build enqueued so far (they may still read the old one)
+        // after every build enqueued so far (they may still read the old one);
+        // none where this TF edit's pass has already run
         std::vector<std::pair<ess_handle, int>> rescans;
         for (Structure *s : sts) {
-            if (s->kind == ESS_NONE || s->p.rescan != 1 || s->p.empty_test != 0) continue;
+            if (s->kind == ESS_NONE || s->p.rescan != 1) continue;
             const std::pair<ess_handle, int> key(s->vol, s->p.brick);
+            Volume &v = get_vol(c, s->vol);
+            auto se = v.scan_epoch.find(s->p.brick);
+            if (v.minmax.count(s->p.brick) && se != v.scan_epoch.end() && se->second == c.edit_epoch)
+                continue;
             if (std::find(rescans.begin(), rescans.end(), key) == rescans.end()) rescans.push_back(key);
         }
+        // every batch stream starts after the builds enqueued on the build
+        // stream so far (they read, and a rescan there writes, Volume::minmax)
+        ESS_CUDA(cudaEventRecord(c.fork_event, c.build_stream));
+        for (cudaStream_t st : c.batch_streams) ESS_CUDA(cudaStreamWaitEvent(st, c.fork_event, 0));
+        c.batch_streams_pending = true;
         cudaStream_t s0 = c.batch_streams[0];
         if (!rescans.empty()) {
-            ESS_CUDA(cudaEventRecord(c.fork_event, c.build_stream));
-            ESS_CUDA(cudaStreamWaitEvent(s0, c.fork_event, 0));
             for (cudaStream_t st : c.batch_streams) {
                 if (st == s0) continue;
                 ESS_CUDA(cudaEventRecord(c.fork_event, st));

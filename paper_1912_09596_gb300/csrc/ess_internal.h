@@ -70,6 +70,9 @@ struct Volume {
     size_t cell_bytes = 0;
     bool use_cells = false;
     std::map<int, float2 *> minmax;  // per brick size: apron min/max (cached)
+    // per brick size: the context's TF-edit epoch at the last rescan (a rescan
+    // is skipped while no TF has changed since: one volume pass per edit)
+    std::map<int, uint64_t> scan_epoch;
     int refs = 0;           // structures using the volume
     bool released = false;
     cudaEvent_t updated = nullptr;  // after the last change of the cell copy
@@ -83,6 +86,9 @@ struct TF {
     int nt;
     float4 *table = nullptr;  // device, nt entries
     int *prefix = nullptr;    // device, nt+1 counts of alpha > 0
+    // device, 2 nt entries: entry i and the float32 difference entry i+1 - i
+    // (0 for the last), the two operands of the renderer's TF lerp
+    float4 *lut = nullptr;
     uint64_t version = 0;     // bumped by every update
     // pinned host copies for asynchronous uploads, used in turn; a slot is
     // rewritten only after the upload that last read it has run
@@ -200,7 +206,16 @@ struct Ctx {
     // too), after one min/max rescan per volume and brick size on the first.
     std::vector<cudaStream_t> batch_streams;
     cudaEvent_t rescan_event = nullptr;
+    // Bumped by every TF upload; a rebuild with `rescan` reads the volume
+    // again only if a TF changed since the last rescan of its (volume, brick).
+    uint64_t edit_epoch = 1;
+    // Set by ess_rebuild_batch: the next build on build_stream first waits for
+    // the batch streams (both read, and rescans write, Volume::minmax).
+    bool batch_streams_pending = false;
     uint32_t *selftest_flag = nullptr;  // device word of ess_selftest_wait
+    // device words: next tile of the streaming kernels, one per stream that
+    // launches them (launches on one stream are ordered, on two they are not)
+    std::map<cudaStream_t, int *> tile_counters;
 
     void *alloc(size_t bytes);
     void free(void *p);
@@ -232,11 +247,17 @@ void launch_check_finite(Ctx &c, const float *v, size_t n);
 size_t cell_array_bytes(const Volume &v);
 void launch_build_cells(Ctx &c, const Volume &v, void *cells);
 void launch_brick_minmax(Ctx &c, const Volume &v, int B, float2 *out);
-void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, int validate);
+// minmax_tma.cu (bricks of 2, 4, 8): false when the volume's layout or brick
+// size does not suit it
+bool launch_brick_minmax_tma(Ctx &c, const Volume &v, int B, float2 *out);
+void launch_tf_prefix(Ctx &c, const float4 *table, int nt, int *prefix, float4 *lut,
+                      int validate);
 void launch_brick_mask(Ctx &c, const float2 *minmax, int64_t nb, const TF &tf,
                        float value_lo, float s, uint8_t *mask);
-void launch_brick_mask_cells(Ctx &c, const Volume &v, int B, const TF &tf, float s,
-                             uint8_t *mask, int gx, int gy, int gz);
+// clears the bricks of a range-test mask that no trilinear cell of theirs
+// makes visible (the exact per-cell vote)
+void launch_vote_bricks(Ctx &c, const Volume &v, int B, const TF &tf, float s, uint8_t *mask,
+                        int gx, int gy, int gz);
 size_t compact_block_count(int64_t nb);
 void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int *count,
                     uint32_t *block_sums, uint32_t *morton_keys, int gx, int gy);

@@ -30,7 +30,8 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.nz = j.vol->nz;
     a.value_lo = j.vol->value_lo;
     a.s = (float)(j.tf->nt - 1) / (j.vol->value_hi - j.vol->value_lo);
-    a.tf = j.tf->table;
+    a.cell_last = (uint32_t)((size_t)(j.vol->nx + 1) * (j.vol->ny + 1) * (j.vol->nz + 1) - 1);
+    a.tf = j.tf->lut;
     a.nt = j.tf->nt;
     for (int i = 0; i < 3; ++i) {
         a.eye[i] = j.cam.eye[i];

@@ -13,8 +13,9 @@ struct RArgs {
     const void *vol;
     const void *cells;   // corner-replicated cells (nullptr: dense sampling only)
     int nx, ny, nz;
+    uint32_t cell_last;  // index of the last cell ((nx+1)(ny+1)(nz+1) - 1 < 2^32)
     float value_lo, s;   // TF coordinate x = (v - value_lo) * s
-    const float4 *tf;
+    const float4 *tf;    // 2 nt entries: entry i, then entry i+1 minus entry i
     int nt;
     float eye[3], u[3], v[3], w[3];
     int ortho;
@@ -163,10 +164,25 @@ template <typename T> struct Corners<T, 0> {
     }
 };
 
-__device__ __forceinline__ size_t cell_index(const RArgs &a, int ix, int iy, int iz)
+// Cell (ix + 1, iy + 1, iz + 1) with each coordinate clamped to [0, n], as
+// the clamp-to-edge reconstruction of R2 reads it.
+__device__ __forceinline__ uint32_t cell_index(const RArgs &a, int ix, int iy, int iz)
 {
     int cx = min(max(ix + 1, 0), a.nx), cy = min(max(iy + 1, 0), a.ny), cz = min(max(iz + 1, 0), a.nz);
-    return (size_t)(cz * (a.ny + 1) + cy) * (size_t)(a.nx + 1) + cx;
+    return (uint32_t)((cz * (a.ny + 1) + cy) * (a.nx + 1) + cx);
+}
+
+// The same cell for a sample of the march, whose position lies in the volume
+// box [0, n] up to rounding: t is in [t_near, t_far) of the exact slab test,
+// and with camera coordinates bounded by 2^16 voxels (checked on the host)
+// the rounding of t and of o + t d stays far below half a voxel, so q = p -
+// 1/2 floors to -1 .. n-1 on every axis and no per-axis clamp can act.  The
+// linear index is still clamped to the array, so no input can read outside
+// it.
+__device__ __forceinline__ uint32_t cell_index_inside(const RArgs &a, int ix, int iy, int iz)
+{
+    const uint32_t i = (uint32_t)(((iz + 1) * (a.ny + 1) + (iy + 1)) * (a.nx + 1) + (ix + 1));
+    return min(i, a.cell_last);
 }
 
 // One trilinear sample (R2) in two steps: fetch() computes the position, the
@@ -175,6 +191,7 @@ __device__ __forceinline__ size_t cell_index(const RArgs &a, int ix, int iy, int
 template <typename T, int SAMPLER> struct CellRaw;
 template <typename T> struct CellRaw<T, 0> {
     float v[8];
+    template <bool INSIDE = false>
     __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
         Corners<T, 0>::get(a, ix, iy, iz, v);
@@ -184,12 +201,26 @@ template <typename T> struct CellRaw<T, 0> {
 #pragma unroll
         for (int k = 0; k < 8; ++k) out[k] = v[k];
     }
+    // the four interpolations along x (R2: x first)
+    __device__ __forceinline__ void xlerp(const RArgs &, float fx, float &c00, float &c10,
+                                          float &c01, float &c11) const
+    {
+        c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+        c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+    }
 };
+template <bool INSIDE>
+__device__ __forceinline__ uint32_t cell_of(const RArgs &a, int ix, int iy, int iz)
+{
+    return INSIDE ? cell_index_inside(a, ix, iy, iz) : cell_index(a, ix, iy, iz);
+}
+
 template <> struct CellRaw<uint8_t, 1> {
     uint2 c;
+    template <bool INSIDE = false>
     __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
-        c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_index(a, ix, iy, iz));
+        c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_of<INSIDE>(a, ix, iy, iz));
     }
     __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
     {
@@ -200,12 +231,21 @@ template <> struct CellRaw<uint8_t, 1> {
             v[4 + k] = __int_as_float(__byte_perm(c.y, 0x4b000000u, 0x7650 | k)) - 8388608.0f;
         }
     }
+    __device__ __forceinline__ void xlerp(const RArgs &a, float fx, float &c00, float &c10,
+                                          float &c01, float &c11) const
+    {
+        float v[8];
+        corners(a, v);
+        c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+        c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+    }
 };
 template <> struct CellRaw<uint16_t, 1> {
     uint4 c;
+    template <bool INSIDE = false>
     __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
-        c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_index(a, ix, iy, iz));
+        c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_of<INSIDE>(a, ix, iy, iz));
     }
     __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
     {
@@ -216,12 +256,22 @@ template <> struct CellRaw<uint16_t, 1> {
             v[2 * k + 1] = __int_as_float(__byte_perm(w[k], 0x4b000000u, 0x7632)) - 8388608.0f;
         }
     }
+    __device__ __forceinline__ void xlerp(const RArgs &a, float fx, float &c00, float &c10,
+                                          float &c01, float &c11) const
+    {
+        float v[8];
+        corners(a, v);
+        c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+        c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+    }
 };
 template <> struct CellRaw<float, 1> {
     float4 c0, c1;
+    template <bool INSIDE = false>
     __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
-        const float4 *p = reinterpret_cast<const float4 *>(a.cells) + 2 * cell_index(a, ix, iy, iz);
+        const float4 *p = reinterpret_cast<const float4 *>(a.cells) +
+                          2 * (size_t)cell_of<INSIDE>(a, ix, iy, iz);
         c0 = __ldg(p);
         c1 = __ldg(p + 1);
     }
@@ -230,15 +280,27 @@ template <> struct CellRaw<float, 1> {
         v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w;
         v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
     }
+    __device__ __forceinline__ void xlerp(const RArgs &a, float fx, float &c00, float &c10,
+                                          float &c01, float &c11) const
+    {
+        float v[8];
+        corners(a, v);
+        c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
+        c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+    }
 };
+
 
 template <typename T, int SAMPLER> struct SampleFetch {
     CellRaw<T, SAMPLER> raw;
     float fx, fy, fz;
+    // a sample of the march (inside the volume box up to rounding)
     __device__ __forceinline__ void fetch(const RArgs &a, const Ray &r, float t)
     {
-        at(a, fmaf(t, r.d[0], r.o[0]), fmaf(t, r.d[1], r.o[1]), fmaf(t, r.d[2], r.o[2]));
+        at<true>(a, fmaf(t, r.d[0], r.o[0]), fmaf(t, r.d[1], r.o[1]), fmaf(t, r.d[2], r.o[2]));
     }
+    // any position (the gradient's neighbours may lie a voxel outside)
+    template <bool INSIDE = false>
     __device__ __forceinline__ void at(const RArgs &a, float px, float py, float pz)
     {
         const float qx = px - 0.5f, qy = py - 0.5f, qz = pz - 0.5f;
@@ -246,21 +308,21 @@ template <typename T, int SAMPLER> struct SampleFetch {
         fx = qx - gxf;
         fy = qy - gyf;
         fz = qz - gzf;
-        raw.load(a, (int)gxf, (int)gyf, (int)gzf);
+        raw.template load<INSIDE>(a, (int)gxf, (int)gyf, (int)gzf);
     }
     __device__ __forceinline__ float value(const RArgs &a) const
     {
-        float v[8];
-        raw.corners(a, v);
-        const float c00 = lerpf(v[0], v[1], fx), c10 = lerpf(v[2], v[3], fx);
-        const float c01 = lerpf(v[4], v[5], fx), c11 = lerpf(v[6], v[7], fx);
+        float c00, c10, c01, c11;
+        raw.xlerp(a, fx, c00, c10, c01, c11);
         const float c0 = lerpf(c00, c10, fy), c1 = lerpf(c01, c11, fy);
         return lerpf(c0, c1, fz);
     }
 };
 
-// The table holds nt + 1 entries, the last a copy of entry nt - 1, so that
-// entry i0 + 1 needs no clamp (with x = nt - 1 the weight w is 0 anyway).
+// The lerp of R5, fmaf(w, c1 - c0, c0) per channel, with the float32
+// difference c1 - c0 read from the table (entry 2 i0 + 1, computed when the TF
+// was uploaded, rounded as the lerp rounds it); the last entry's difference is
+// 0 (entry i1 = min(i0 + 1, nt - 1)).
 __device__ __forceinline__ float4 classify(const RArgs &a, float v)
 {
     float x = (v - a.value_lo) * a.s;
@@ -268,9 +330,9 @@ __device__ __forceinline__ float4 classify(const RArgs &a, float v)
     x = fminf(fmaxf(x, 0.0f), xmax);  // x is finite
     int i0 = (int)x;
     float w = x - (float)i0;
-    float4 c0 = __ldg(a.tf + i0), c1 = __ldg(a.tf + i0 + 1);
-    return make_float4(fmaf(w, c1.x - c0.x, c0.x), fmaf(w, c1.y - c0.y, c0.y),
-                       fmaf(w, c1.z - c0.z, c0.z), fmaf(w, c1.w - c0.w, c0.w));
+    float4 c0 = __ldg(a.tf + 2 * i0), d = __ldg(a.tf + 2 * i0 + 1);
+    return make_float4(fmaf(w, d.x, c0.x), fmaf(w, d.y, c0.y), fmaf(w, d.z, c0.z),
+                       fmaf(w, d.w, c0.w));
 }
 
 // ------------------------------------------- second workload (R13, R14)
@@ -684,44 +746,59 @@ struct Ranges {
     }
 };
 
-// Interval-by-interval skipping with phases: collect, then march.  The outer
-// loop is uniform over the lanes that entered together (__any_sync), and the
-// inner loops have single exits, so the warp reconverges at every phase
-// boundary.
+// Interval-by-interval skipping in rounds.  Every lane keeps a queue of up to
+// RANGES sample-index ranges (rule S, with the monotone cursor k_next; ranges
+// that touch are merged) holding `held` samples.  A round first tops each
+// queue up from the walker (lanes whose queue is full skip that), then every
+// live lane of the warp marches the same number m of samples, m the smallest
+// holding among them, so that no lane idles in the march unless its ray ends
+// or terminates early; leftovers stay queued.  Samples are still taken in
+// increasing k, exactly as interval-by-interval marching takes them.  The
+// round loop is uniform over the lanes that entered together (m is a warp
+// reduction) and its inner loops have single exits.
 template <typename T, int SAMPLER, int SHADE, typename Walk>
 __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float tn, float tf,
                                            Walk &w, Acc &acc, int &ns)
 {
     const unsigned lanes = __activemask();
-    int k_next = 0;
+    int k_next = 0;       // first sample index not queued yet
+    int held = 0;         // samples queued
+    int k = 0;            // next sample to march: the front range's cursor
+    bool walking = true;  // the walker may still yield intervals
     bool alive = true;
-    while (__any_sync(lanes, alive)) {
-        Ranges rg;
-        rg.clear();
-        if (alive) {
-            int held = 0;
+    Ranges rg;
+    rg.clear();
+    while (true) {
+        if (alive && walking) {
             float ta, tb;
             while (rg.n < RANGES && held < LOOKAHEAD) {
-                if (!w.next(a, r, tn, tf, ta, tb)) break;
+                if (!w.next(a, r, tn, tf, ta, tb)) {
+                    walking = false;
+                    break;
+                }
                 float ka = ceilf((ta - tn) / a.dt) - 1.0f;
                 float kb = floorf((tb - tn) / a.dt) + 1.0f;
                 kb = kb < 16777216.0f ? kb : 16777216.0f;
                 int k0 = ka > (float)k_next ? (int)ka : k_next;
                 int k1 = (int)kb;
                 if (k1 >= k0) {
-                    if (rg.n > 0 && k0 == k_next) rg.extend_last(k1);  // touches the previous range
-                    else rg.append(k0, k1);
+                    if (rg.n > 0 && k0 == k_next) {
+                        rg.extend_last(k1);  // touches the previous range
+                    } else {
+                        if (rg.n == 0) k = k0;
+                        rg.append(k0, k1);
+                    }
                     held += k1 - k0 + 1;
                     k_next = k1 + 1;
                 }
             }
-            if (rg.n == 0) alive = false;
         }
+        if (held == 0) alive = false;
+        const int m = __reduce_min_sync(lanes, alive ? held : 0x7fffffff);
+        if (m == 0x7fffffff) break;  // every lane's ray is done
         if (alive) {
-            // march the collected ranges in increasing k
-            int k = rg.r0.x;
             float kf = (float)k;
-            while (true) {
+            for (int j = 0; j < m; ++j) {
                 const float t = fmaf(kf, a.dt, tn);
                 if (!(t < tf)) {
                     alive = false;
@@ -736,14 +813,14 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
                 }
                 if (k == rg.r0.y) {
                     rg.pop_front();
-                    if (rg.n == 0) break;
-                    k = rg.r0.x;
+                    k = rg.r0.x;  // meaningless once the queue is empty (held is 0 then)
                     kf = (float)k;
                 } else {
                     ++k;
                     kf += 1.0f;
                 }
             }
+            held -= m;
         }
     }
 }

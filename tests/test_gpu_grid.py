@@ -75,6 +75,7 @@ def test_minmax_vector_rows_and_rescan(gpu, ctx, ora, case, B):
     ref = ora.brick_mask(rmin, rmax, ot, lo, hi)
     for rescan in (1, 0, 1):
         st = ess.ess_build(ctx, vol, t, ess.GRID, ess.build_params(brick=B, rescan=rescan))
+        ess.ess_tf_update(ctx, t, torch.from_numpy(tf).cuda())   # an edit: the pass runs again
         ess.ess_rebuild(ctx, st)
         mm = ess.ess_structure_read(ctx, st, ess.ARR_MINMAX).reshape(-1, 2)
         assert np.array_equal(bits(mm[:, 0]), bits(rmin)) and np.array_equal(bits(mm[:, 1]), bits(rmax))
@@ -211,3 +212,37 @@ def test_dense_and_cell_samplers_agree(gpu, ctx, ora, case):
         assert_image_parity(imgs[0], ref, name)
         for im in imgs[1:]:
             assert np.array_equal(bits(im), bits(imgs[0]))
+
+
+def test_rescan_once_per_tf_edit(gpu, ctx, ora):
+    """With rescan, the volume is read once per TF edit (Sec. 3.1 classifies
+    after each edit), and the grid, LBVH and k-d rebuilt for that edit share
+    the pass: one min/max launch per edit and brick size, none when nothing
+    was edited, one more per further brick size; masks still equal the
+    oracle's."""
+    ess, torch = gpu
+    v = synth.ct_like_u8((96, 80, 72), seed=2, n_vessels=5)
+    tfs = synth.tf_set_ct()
+    vol, t = upload(ess, torch, ctx, v, 0, 255, tfs[0])
+    kd = dict(nbins=4, halting=1, mls=32)
+    sts = [ess.ess_build(ctx, vol, t, k, ess.build_params(brick=8, rescan=1, **kd))
+           for k in (ess.GRID, ess.LBVH, ess.KD)]
+    other = ess.ess_build(ctx, vol, t, ess.GRID, ess.build_params(brick=16, rescan=1))
+    ess.ess_sync(ctx)
+    ess.ess_profile_reset(ctx)
+    ess.ess_profile_enable(ctx, True)
+    for ti in (1, 2, 3):
+        ess.ess_tf_update(ctx, t, torch.from_numpy(tfs[ti]).cuda())
+        for st in sts:
+            ess.ess_rebuild(ctx, st)
+    for st in sts:                     # no edit since: the last pass stands
+        ess.ess_rebuild(ctx, st)
+    ess.ess_rebuild(ctx, other)        # another brick size: its own pass
+    ess.ess_rebuild_batch(ctx, sts)    # the batch finds this edit's pass done
+    ess.ess_sync(ctx)
+    ess.ess_profile_enable(ctx, False)
+    assert ess.ess_profile_read(ctx)["brick_minmax"][0] == 4
+    ov, ot = ora.OVolume(v, 0, 255), ora.OTF(tfs[3])
+    for st, B in zip(sts + [other], (8, 8, 8, 16)):
+        assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_MASK), ora.build_mask(ov, ot, B))
+        ess.ess_release(ctx, st)
