@@ -144,6 +144,8 @@ struct Structure {
     uint32_t *kd_block_sums = nullptr;
     size_t kd_bs_cap = 0;
     void *kd_state = nullptr;                   // device level state (32 bytes)
+    unsigned long long *kd_chunk = nullptr;     // look-back words of the 4-bin decide/emit
+    size_t kd_chunk_cap = 0;
     cudaGraph_t kd_graph = nullptr;             // device-driven build (binned planes)
     cudaGraphExec_t kd_exec = nullptr;
     size_t device_bytes = 0;

@@ -130,7 +130,8 @@ struct KdState {
     int levels;      // levels started so far; the current level is number `levels`
     int splits;      // splits on the current level
     unsigned done;   // emit blocks finished on the current level
-    int pad[2];
+    unsigned epoch;  // bumped by every build: tags the look-back words of its levels
+    int pad;
 };
 
 // Slab buffer of the current level (parity of the level number) and of the next.
@@ -155,6 +156,7 @@ __global__ void k_kd_root_init(int32_t *root_box, KdState *st)
         st->levels = 0;
         st->splits = 0;
         st->done = 0;
+        st->epoch += 1;
     }
 }
 
@@ -443,18 +445,36 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
 // candidate of lane (a, j), 1 <= j < ns, costs V(L) + V(R), and the argmin
 // over the half takes the lowest (axis, plane) among equal costs, as the
 // per-thread form does.  Integer arithmetic only, so the decisions are the
-// same.  Split counts per 256 nodes are added atomically (the emit kernel's
-// last block zeroes them for the next level).
+// same.
+//
+// The same kernel emits the children.  A block takes chunks of 16
+// consecutive nodes (one per half-warp) in increasing order; the split count
+// of chunk c is chained to the chunks before it by a decoupled look-back (one
+// 64-bit word per chunk: the level's tag, a flag and the count or prefix), so
+// the children of chunk c are numbered right after those of chunks < c, in
+// breadth-first order.  The last block to finish moves the level state on.
 __device__ __forceinline__ bool box_nonempty(const int32_t *b) { return b[0] != INT_MAX; }
 
-__global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ nodes9,
-                                                    int32_t *slabs0, int32_t *slabs1, KdDecision *dec,
-                                                    uint32_t *block_counts, const KdState *st,
-                                                    KdParams P, int next_cap)
+constexpr int KD_CHUNK = 16;                    // nodes per look-back chunk
+constexpr unsigned long long KD_LB_AGG = 1ull << 30, KD_LB_INC = 2ull << 30;
+constexpr unsigned long long KD_LB_MASK = (1ull << 30) - 1;
+constexpr long KD_LB_SPIN_LIMIT = 1l << 24;
+
+__global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_t *slabs0,
+                                                         int32_t *slabs1,
+                                                         unsigned long long *chunk_st, KdState *st,
+                                                         KdParams P, int next_cap, int capacity,
+                                                         int max_levels, uint32_t *status,
+                                                         cudaGraphConditionalHandle handle,
+                                                         int use_handle)
 {
     constexpr int S = 4;
     const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
-    if (lvl_size <= 0) return;  // uniform
+    if (lvl_size <= 0) {  // uniform: the tree is done
+        if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0u);
+        return;
+    }
+    const unsigned long long tag = ((unsigned long long)((st->epoch << 8) | (unsigned)st->levels)) << 32;
     {
         // the next level has at most min(2 lvl_size, capacity) nodes
         int2 *next = reinterpret_cast<int2 *>(kd_next_slabs(slabs0, slabs1, st));
@@ -468,10 +488,11 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int a = (hl >> 2) < 3 ? hl >> 2 : 0, j = hl & 3;
     const bool slab_lane = hl < 12;
-    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    for (int base = 2 * gw; base < lvl_size; base += 2 * warps) {  // uniform per warp
-        const int l = base + half;
+    __shared__ KdDecision sdec[KD_CHUNK];
+    __shared__ int s_excl;
+    const int nchunks = (lvl_size + KD_CHUNK - 1) / KD_CHUNK;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {  // uniform per block
+        const int l = ch * KD_CHUNK + 2 * (threadIdx.x >> 5) + half;
         const bool node = l < lvl_size;
         const int32_t *X = nodes9 + 9 * (size_t)(lvl_begin + (node ? l : 0));
         int32_t x[6];
@@ -555,12 +576,12 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
             dl[k] = __shfl_sync(0xffffffffu, L[k], src);
             dr[k] = __shfl_sync(0xffffffffu, suf[k], src);
         }
-        if (hl == 0 && node) {
+        if (hl == 0) {
             KdDecision d;
             d.split = 0;
             d.axis = -1;
             d.plane = 0;
-            if (bax >= 0 && box_nonempty(dl) && box_nonempty(dr)) {
+            if (node && bax >= 0 && box_nonempty(dl) && box_nonempty(dr)) {
                 d.split = 1;
                 d.axis = bax;
                 d.plane = bpl;
@@ -569,11 +590,88 @@ __global__ void __launch_bounds__(256) k_kd_decide4(const int32_t *__restrict__ 
                     d.L[k] = dl[k];
                     d.R[k] = dr[k];
                 }
-                atomicAdd(block_counts + (l >> 8), 1u);
             }
-            dec[l] = d;
+            sdec[l - ch * KD_CHUNK] = d;
         }
+        __syncthreads();
+        // the chunk's split count, chained to the chunks before it
+        if (threadIdx.x < 32) {
+            const unsigned ball = __ballot_sync(0xffffffffu, lane < KD_CHUNK && sdec[lane].split);
+            if (lane == 0) {
+                const unsigned long long cnt = (unsigned long long)__popc(ball);
+                volatile unsigned long long *cs = chunk_st;
+                unsigned long long excl = 0;
+                if (ch > 0) {
+                    cs[ch] = tag | KD_LB_AGG | cnt;
+                    for (int j = ch - 1; j >= 0; --j) {
+                        unsigned long long v = 0;
+                        long spins = 0;
+                        while (((v = cs[j]) & ~(KD_LB_MASK | KD_LB_AGG | KD_LB_INC)) != tag ||
+                               (v & (KD_LB_AGG | KD_LB_INC)) == 0ull) {
+                            if (++spins > KD_LB_SPIN_LIMIT) break;
+                        }
+                        if (spins > KD_LB_SPIN_LIMIT) {
+                            atomicOr(status, DEV_ERR_TIMEOUT);
+                            break;
+                        }
+                        excl += v & KD_LB_MASK;
+                        if (v & KD_LB_INC) break;
+                    }
+                }
+                __threadfence();
+                cs[ch] = tag | KD_LB_INC | (excl + cnt);
+                s_excl = (int)excl;
+                if (ch == nchunks - 1) st->splits = (int)(excl + cnt);
+            }
+        }
+        __syncthreads();
+        // emit: children of the chunk's split nodes, numbered in node order
+        if (threadIdx.x < KD_CHUNK && sdec[threadIdx.x].split) {
+            int rank = 0;
+            for (int k = 0; k < (int)threadIdx.x; ++k) rank += sdec[k].split;
+            const int fc = lvl_begin + lvl_size + 2 * (s_excl + rank);
+            if (fc + 1 >= capacity) {
+                atomicOr(status, DEV_ERR_OVERFLOW);
+            } else {
+                const KdDecision &d = sdec[threadIdx.x];
+                int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + ch * KD_CHUNK + threadIdx.x);
+                rec[6] = d.axis;
+                rec[7] = d.plane;
+                rec[8] = fc;
+                int32_t *cl = nodes9 + 9 * (size_t)fc;
+                int32_t *cr = cl + 9;
+                for (int k = 0; k < 6; ++k) {
+                    cl[k] = d.L[k];
+                    cr[k] = d.R[k];
+                }
+                cl[6] = cr[6] = -1;
+                cl[7] = cr[7] = 0;
+                cl[8] = cr[8] = -1;
+            }
+        }
+        __syncthreads();  // sdec and s_excl are rewritten by the next chunk
     }
+    // the last block to finish advances the level
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    st->done = 0;
+    int next = 2 * *(volatile int *)&st->splits;
+    st->prev_begin = lvl_begin;
+    st->lvl_begin = lvl_begin + lvl_size;
+    st->levels += 1;
+    if (next > 0 && (st->lvl_begin + next > capacity || st->levels >= max_levels)) {
+        atomicOr(status, DEV_ERR_OVERFLOW);
+        next = 0;
+    }
+    st->lvl_size = next;
+    st->splits = 0;
+    if (use_handle) cudaGraphSetConditional(handle, next > 0 ? 1u : 0u);
 }
 
 // Sum of v over the block (256 threads).
@@ -761,10 +859,26 @@ void kd_reserve(Ctx &c, Structure &s, int lvl_size, int S, int cur)
         ESS_CUDA(cudaMemsetAsync(s.kd_block_sums, 0, sizeof(uint32_t) * s.kd_bs_cap, c.stream));
 }
 
+// Look-back words of the fused 4-bin step: one per chunk of the widest level
+// (at most one node per non-empty brick), zeroed once (they carry the tag of
+// the build and level that wrote them).
+static void kd_chunk_reserve(Ctx &c, Structure &s)
+{
+    const size_t need = (size_t)(s.nb + KD_CHUNK - 1) / KD_CHUNK + 2;
+    if (s.kd_chunk_cap >= need) return;
+    c.free(s.kd_chunk);
+    s.kd_chunk = (unsigned long long *)c.alloc(need * sizeof(unsigned long long));
+    s.kd_chunk_cap = need;
+    ESS_CUDA(cudaMemsetAsync(s.kd_chunk, 0, need * sizeof(unsigned long long), c.stream));
+}
+
 void kd_free(Ctx &c, Structure &s)
 {
-    void *ptrs[] = {s.kd_slabs[0], s.kd_slabs[1], s.kd_vr, s.kd_dec, s.kd_block_sums};
+    void *ptrs[] = {s.kd_slabs[0], s.kd_slabs[1], s.kd_vr, s.kd_dec, s.kd_block_sums,
+                    s.kd_chunk};
     for (void *p : ptrs) c.free(p);
+    s.kd_chunk = nullptr;
+    s.kd_chunk_cap = 0;
     s.kd_slabs[0] = s.kd_slabs[1] = nullptr;
     s.kd_vr = nullptr;
     s.kd_dec = nullptr;
@@ -803,14 +917,15 @@ static void kd_level_launches(Ctx &c, Structure &s, const KdParams &P, unsigned 
         k_kd_accumulate<0><<<brick_blocks, 256, 0, c.stream>>>(s.ids, s.count, s.brick_node,
                                                                s.kd_nodes, s.kd_slabs[0],
                                                                s.kd_slabs[1], st, P);
-    if (P.S == 4)
-        k_kd_decide4<<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
-                                                        (KdDecision *)s.kd_dec, s.kd_block_sums, st,
-                                                        P, next_cap);
-    else
-        k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
-                                                          s.kd_vr, (KdDecision *)s.kd_dec,
-                                                          s.kd_block_sums, st, P, next_cap);
+    if (P.S == 4) {  // decide and emit in one kernel
+        k_kd_decide_emit4<<<emit_blocks, 256, 0, c.stream>>>(
+            s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1], s.kd_chunk, st, P, next_cap, s.kd_capacity,
+            KD_MAX_LEVELS, c.dev_status, h, use_handle);
+        return;
+    }
+    k_kd_decide<0><<<node_blocks, 256, 0, c.stream>>>(s.kd_nodes, s.kd_slabs[0], s.kd_slabs[1],
+                                                      s.kd_vr, (KdDecision *)s.kd_dec,
+                                                      s.kd_block_sums, st, P, next_cap);
     k_kd_emit<<<emit_blocks, 256, 0, c.stream>>>((const KdDecision *)s.kd_dec, s.kd_block_sums,
                                                  s.kd_nodes, s.kd_capacity, KD_MAX_LEVELS,
                                                  c.dev_status, st, h, use_handle);
@@ -858,6 +973,7 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
     void *bs = s.kd_block_sums;
     grow(c, bs, s.kd_bs_cap, (cap + 255) / 256, sizeof(uint32_t));
     s.kd_block_sums = (uint32_t *)bs;
+    kd_chunk_reserve(c, s);
     if (!c.capture_stream)
         ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
 
@@ -938,6 +1054,7 @@ void launch_kd(Ctx &c, Structure &s)
         return;
     }
     // host-driven level loop (exhaustive planes or buffers too large)
+    if (P.S == 4) kd_chunk_reserve(c, s);
     int64_t n_cap = s.nb;
     const unsigned brick_blocks = (unsigned)((n_cap + 255) / 256);
     if (s.kd_slab_cap[0] < 16) {

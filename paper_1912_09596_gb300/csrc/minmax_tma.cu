@@ -58,19 +58,16 @@ __device__ __forceinline__ uint32_t tma_max_h2(uint32_t a, uint32_t b)
     return d;
 }
 
-// Column-wise min/max of the 16-byte blocks of one column block over rows,
-// and of one apron column (from the apron copies).
+// Column-wise min/max of the 16-byte blocks of one column block over rows.
 template <typename T> struct Cols;
 template <> struct Cols<uint8_t> {
     // byte b under the high byte 0x64 is the half 1024 + b, ordered as b:
     // word i gives the pairs (b0, b1) and (b2, b3) = columns 4i.. 4i+3
     uint32_t mna[4], mnb[4], mxa[4], mxb[4];
-    uint32_t emn, emx;
     __device__ __forceinline__ void init()
     {
 #pragma unroll
         for (int i = 0; i < 4; ++i) mna[i] = mnb[i] = 0x64ff64ffu, mxa[i] = mxb[i] = 0x64006400u;
-        emn = 0xffu, emx = 0u;
     }
     __device__ __forceinline__ void add(const uint4 &w)
     {
@@ -85,12 +82,6 @@ template <> struct Cols<uint8_t> {
             mxb[i] = tma_max_h2(mxb[i], b);
         }
     }
-    // last = true: the block's last voxel (the column left of the chunk)
-    __device__ __forceinline__ void apron(const uint4 &w, bool last)
-    {
-        const uint32_t v = last ? w.w >> 24 : w.x & 0xffu;
-        emn = min(emn, v), emx = max(emx, v);
-    }
     __device__ __forceinline__ void columns(float *mn, float *mx) const
     {
 #pragma unroll
@@ -101,8 +92,6 @@ template <> struct Cols<uint8_t> {
             mx[4 * i + 2] = (float)(mxb[i] & 0xffu), mx[4 * i + 3] = (float)((mxb[i] >> 16) & 0xffu);
         }
     }
-    __device__ __forceinline__ float apron_min() const { return (float)emn; }
-    __device__ __forceinline__ float apron_max() const { return (float)emx; }
     // merge with lane ^ o of the warp
     __device__ __forceinline__ void shfl_merge(int o)
     {
@@ -113,18 +102,14 @@ template <> struct Cols<uint8_t> {
             mxa[i] = tma_max_h2(mxa[i], __shfl_xor_sync(0xffffffffu, mxa[i], o));
             mxb[i] = tma_max_h2(mxb[i], __shfl_xor_sync(0xffffffffu, mxb[i], o));
         }
-        emn = min(emn, __shfl_xor_sync(0xffffffffu, emn, o));
-        emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
     }
 };
 template <> struct Cols<uint16_t> {
     uint32_t mn[8], mx[8];
-    uint32_t emn, emx;
     __device__ __forceinline__ void init()
     {
 #pragma unroll
         for (int j = 0; j < 8; ++j) mn[j] = 0xffffu, mx[j] = 0u;
-        emn = 0xffffu, emx = 0u;
     }
     __device__ __forceinline__ void add(const uint4 &w)
     {
@@ -136,18 +121,11 @@ template <> struct Cols<uint16_t> {
             mn[2 * i + 1] = min(mn[2 * i + 1], hi), mx[2 * i + 1] = max(mx[2 * i + 1], hi);
         }
     }
-    __device__ __forceinline__ void apron(const uint4 &w, bool last)
-    {
-        const uint32_t v = last ? w.w >> 16 : w.x & 0xffffu;
-        emn = min(emn, v), emx = max(emx, v);
-    }
     __device__ __forceinline__ void columns(float *cmn, float *cmx) const
     {
 #pragma unroll
         for (int j = 0; j < 8; ++j) cmn[j] = (float)mn[j], cmx[j] = (float)mx[j];
     }
-    __device__ __forceinline__ float apron_min() const { return (float)emn; }
-    __device__ __forceinline__ float apron_max() const { return (float)emx; }
     __device__ __forceinline__ void shfl_merge(int o)
     {
 #pragma unroll
@@ -155,18 +133,14 @@ template <> struct Cols<uint16_t> {
             mn[j] = min(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
             mx[j] = max(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
         }
-        emn = min(emn, __shfl_xor_sync(0xffffffffu, emn, o));
-        emx = max(emx, __shfl_xor_sync(0xffffffffu, emx, o));
     }
 };
 template <> struct Cols<float> {
     float mn[4], mx[4];
-    float emn, emx;
     __device__ __forceinline__ void init()
     {
 #pragma unroll
         for (int j = 0; j < 4; ++j) mn[j] = INFINITY, mx[j] = -INFINITY;
-        emn = INFINITY, emx = -INFINITY;
     }
     __device__ __forceinline__ void add(const uint4 &w)
     {
@@ -175,18 +149,11 @@ template <> struct Cols<float> {
 #pragma unroll
         for (int j = 0; j < 4; ++j) mn[j] = fminf(q[j], mn[j]), mx[j] = fmaxf(q[j], mx[j]);
     }
-    __device__ __forceinline__ void apron(const uint4 &w, bool last)
-    {
-        const float v = __uint_as_float(last ? w.w : w.x);
-        emn = fminf(v, emn), emx = fmaxf(v, emx);
-    }
     __device__ __forceinline__ void columns(float *cmn, float *cmx) const
     {
 #pragma unroll
         for (int j = 0; j < 4; ++j) cmn[j] = mn[j], cmx[j] = mx[j];
     }
-    __device__ __forceinline__ float apron_min() const { return emn; }
-    __device__ __forceinline__ float apron_max() const { return emx; }
     __device__ __forceinline__ void shfl_merge(int o)
     {
 #pragma unroll
@@ -194,8 +161,6 @@ template <> struct Cols<float> {
             mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
             mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
         }
-        emn = fminf(emn, __shfl_xor_sync(0xffffffffu, emn, o));
-        emx = fmaxf(emx, __shfl_xor_sync(0xffffffffu, emx, o));
     }
 };
 
