@@ -189,7 +189,8 @@ def fp32_peak_tflops(sms):
 # source files that define each kernel (by profiling-name prefix); every
 # kernel also depends on the shared internal header
 KERNEL_FILES = (("render_shaded", ("render_shaded.cu", "render_kernels.h")),
-                ("render", ("render.cu", "render_kernels.h")), ("brick_", ("classify.cu",)),
+                ("render", ("render.cu", "render_kernels.h")),
+                ("brick_minmax", ("classify.cu", "minmax_tma.cu")), ("brick_", ("classify.cu",)),
                 ("compact", ("classify.cu",)), ("tf_prefix", ("classify.cu",)),
                 ("vote_bricks", ("classify.cu",)), ("build_cells", ("classify.cu",)),
                 ("check_finite", ("classify.cu",)), ("sort", ("lbvh.cu",)),
