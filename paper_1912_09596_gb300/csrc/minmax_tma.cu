@@ -57,6 +57,19 @@ __device__ __forceinline__ uint32_t tma_max_h2(uint32_t a, uint32_t b)
     asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
+// two 16-bit unsigned lanes per word
+__device__ __forceinline__ uint32_t tma_min_u2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t tma_max_u2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
 
 // Column-wise min/max of the 16-byte blocks of one column block over rows.
 template <typename T> struct Cols;
@@ -105,33 +118,34 @@ template <> struct Cols<uint8_t> {
     }
 };
 template <> struct Cols<uint16_t> {
-    uint32_t mn[8], mx[8];
+    // word i holds columns 2i (low half) and 2i+1 (high half), as the voxels
+    // lie in the row: one min.u16x2 and one max.u16x2 per two voxels
+    uint32_t mn[4], mx[4];
     __device__ __forceinline__ void init()
     {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) mn[j] = 0xffffu, mx[j] = 0u;
+        for (int i = 0; i < 4; ++i) mn[i] = 0xffffffffu, mx[i] = 0u;
     }
     __device__ __forceinline__ void add(const uint4 &w)
     {
         const uint32_t q[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t lo = q[i] & 0xffffu, hi = q[i] >> 16;
-            mn[2 * i] = min(mn[2 * i], lo), mx[2 * i] = max(mx[2 * i], lo);
-            mn[2 * i + 1] = min(mn[2 * i + 1], hi), mx[2 * i + 1] = max(mx[2 * i + 1], hi);
-        }
+        for (int i = 0; i < 4; ++i) mn[i] = tma_min_u2(mn[i], q[i]), mx[i] = tma_max_u2(mx[i], q[i]);
     }
     __device__ __forceinline__ void columns(float *cmn, float *cmx) const
     {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cmn[j] = (float)mn[j], cmx[j] = (float)mx[j];
+        for (int i = 0; i < 4; ++i) {
+            cmn[2 * i] = (float)(mn[i] & 0xffffu), cmn[2 * i + 1] = (float)(mn[i] >> 16);
+            cmx[2 * i] = (float)(mx[i] & 0xffffu), cmx[2 * i + 1] = (float)(mx[i] >> 16);
+        }
     }
     __device__ __forceinline__ void shfl_merge(int o)
     {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            mn[j] = min(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], o));
-            mx[j] = max(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], o));
+        for (int i = 0; i < 4; ++i) {
+            mn[i] = tma_min_u2(mn[i], __shfl_xor_sync(0xffffffffu, mn[i], o));
+            mx[i] = tma_max_u2(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
         }
     }
 };

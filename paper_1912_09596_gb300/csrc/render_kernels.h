@@ -469,7 +469,10 @@ __device__ __forceinline__ void trace_naive(const RArgs &a, const Ray &r, float 
 // ---------------------------------------------------------- walkers
 // A walker yields the hit intervals [ta, tb] of the non-empty regions of a
 // ray in ray order: the DDA over the brick raster (macrocell grid) or the
-// ordered traversal of a box tree.  The renderer alternates between a
+// ordered traversal of a box tree.  Its step() takes one cell or node and
+// reports an interval when that cell or leaf is non-empty, so that a lane
+// that has found an interval goes on to the next one while the other lanes
+// of its warp are still stepping.  The renderer alternates between a
 // collection phase, in which the walker's next intervals become sample-index
 // ranges (rule S, with the monotone cursor k_next; ranges that touch are
 // merged), and a marching phase over the collected ranges.  Lanes of a warp
@@ -517,38 +520,38 @@ struct GridWalk {
         done = false;
     }
 
-    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+    // One cell of the walk: true when the cell is non-empty ([ta, tb] its
+    // span); sets `done` after the last cell.
+    __device__ __forceinline__ bool step(const RArgs &a, const Ray &r, float, float tf, float &ta,
                                          float &tb)
     {
+        if (--left < 0) {
+            done = true;
+            return false;
+        }
         const int B = a.B;
         bool hit = false;
-        while (!done && !hit) {
-            if (--left < 0) {
-                done = true;
-                break;
-            }
-            float texit = fminf(tx, fminf(ty, tz));
-            if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
-                ta = tcur;
-                tb = fminf(texit, tf);
-                hit = true;
-            }
-            if (!(texit <= tf)) done = true;
-            if (tx <= ty && tx <= tz) {
-                cx += sx;
-                if (cx < 0 || cx >= a.gx) done = true;
-                tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
-            } else if (ty <= tz) {
-                cy += sy;
-                if (cy < 0 || cy >= a.gy) done = true;
-                ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
-            } else {
-                cz += sz;
-                if (cz < 0 || cz >= a.gz) done = true;
-                tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
-            }
-            tcur = texit;
+        float texit = fminf(tx, fminf(ty, tz));
+        if (__ldg(a.mask + ((size_t)(cz * a.gy + cy) * a.gx + cx))) {
+            ta = tcur;
+            tb = fminf(texit, tf);
+            hit = true;
         }
+        if (!(texit <= tf)) done = true;
+        if (tx <= ty && tx <= tz) {
+            cx += sx;
+            if (cx < 0 || cx >= a.gx) done = true;
+            tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
+        } else if (ty <= tz) {
+            cy += sy;
+            if (cy < 0 || cy >= a.gy) done = true;
+            ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
+        } else {
+            cz += sz;
+            if (cz < 0 || cz >= a.gz) done = true;
+            tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
+        }
+        tcur = texit;
         return hit;
     }
 };
@@ -606,62 +609,60 @@ template <int KIND, int STACK> struct TreeWalk {
         }
     }
 
-    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+    // One node of the traversal: true when it is a leaf ([ta, tb] its
+    // interval); sets `done` when the stack runs out.
+    __device__ __forceinline__ bool step(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
                                          float &tb)
     {
-        bool hit = false;
-        while (!done && !hit) {
-            if (--budget < 0) {
-                done = true;
-                break;
-            }
-            if (ref < 0) {
-                if (-1 - (int64_t)ref < n_leaf) {
-                    ta = cta;
-                    tb = ctb;
-                    hit = true;
-                    pop();
-                } else {
-                    done = true;
-                }
-                continue;
-            }
-            if (ref >= n_inner) {
-                done = true;
-                break;
-            }
-            const float4 *q = reinterpret_cast<const float4 *>(a.nodes + ref);
-            float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
-            int4 q3 = __ldg(reinterpret_cast<const int4 *>(q + 3));
-            const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
-            const float rlo[3] = {q1.z, q1.w, q2.x}, rhi[3] = {q2.y, q2.z, q2.w};
-            float la = tn, lb = tf, ra = tn, rb = tf;
-            slab_tree(r, llo, lhi, la, lb);
-            slab_tree(r, rlo, rhi, ra, rb);
-            bool hl = la <= lb, hr = ra <= rb;
-            if (hl && hr) {
-                bool left_first = la <= ra;
-                if (sp < STACK) {
-                    stk[sp] = left_first ? make_float4(__int_as_float(q3.y), ra, rb, 0.0f)
-                                         : make_float4(__int_as_float(q3.x), la, lb, 0.0f);
-                    ++sp;
-                }
-                ref = left_first ? q3.x : q3.y;
-                cta = left_first ? la : ra;
-                ctb = left_first ? lb : rb;
-            } else if (hl) {
-                ref = q3.x;
-                cta = la;
-                ctb = lb;
-            } else if (hr) {
-                ref = q3.y;
-                cta = ra;
-                ctb = rb;
-            } else {
-                pop();
-            }
+        if (--budget < 0) {
+            done = true;
+            return false;
         }
-        return hit;
+        if (ref < 0) {
+            if (-1 - (int64_t)ref < n_leaf) {
+                ta = cta;
+                tb = ctb;
+                pop();
+                return true;
+            }
+            done = true;
+            return false;
+        }
+        if (ref >= n_inner) {
+            done = true;
+            return false;
+        }
+        const float4 *q = reinterpret_cast<const float4 *>(a.nodes + ref);
+        float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+        int4 q3 = __ldg(reinterpret_cast<const int4 *>(q + 3));
+        const float llo[3] = {q0.x, q0.y, q0.z}, lhi[3] = {q0.w, q1.x, q1.y};
+        const float rlo[3] = {q1.z, q1.w, q2.x}, rhi[3] = {q2.y, q2.z, q2.w};
+        float la = tn, lb = tf, ra = tn, rb = tf;
+        slab_tree(r, llo, lhi, la, lb);
+        slab_tree(r, rlo, rhi, ra, rb);
+        bool hl = la <= lb, hr = ra <= rb;
+        if (hl && hr) {
+            bool left_first = la <= ra;
+            if (sp < STACK) {
+                stk[sp] = left_first ? make_float4(__int_as_float(q3.y), ra, rb, 0.0f)
+                                     : make_float4(__int_as_float(q3.x), la, lb, 0.0f);
+                ++sp;
+            }
+            ref = left_first ? q3.x : q3.y;
+            cta = left_first ? la : ra;
+            ctb = left_first ? lb : rb;
+        } else if (hl) {
+            ref = q3.x;
+            cta = la;
+            ctb = lb;
+        } else if (hr) {
+            ref = q3.y;
+            cta = ra;
+            ctb = rb;
+        } else {
+            pop();
+        }
+        return false;
     }
 };
 
@@ -676,33 +677,36 @@ struct HybridWalk {
     GridWalk grid;
     float leaf_tb;
     bool in_leaf;
+    bool done;
 
     __device__ __forceinline__ void init(const RArgs &a, const Ray &r, float tn, float tf)
     {
         tree.init(a, r, tn, tf);
         in_leaf = false;
+        done = tree.done;
     }
 
-    __device__ __forceinline__ bool next(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
+    // One step of the walk: a brick of the current leaf, or a tree node
+    // while no leaf is open; true for a non-empty brick ([ta, tb] its span).
+    __device__ __forceinline__ bool step(const RArgs &a, const Ray &r, float tn, float tf, float &ta,
                                          float &tb)
     {
-        bool hit = false;
-        bool more = true;
-        while (!hit && more) {
-            if (in_leaf) {
-                hit = grid.next(a, r, tn, leaf_tb, ta, tb);
-                if (!hit) in_leaf = false;
-            } else {
-                float la, lb;
-                more = tree.next(a, r, tn, tf, la, lb);
-                if (more) {
-                    grid.init(a, r, la);
-                    leaf_tb = lb;
-                    in_leaf = true;
-                }
+        if (in_leaf) {
+            const bool hit = grid.step(a, r, tn, leaf_tb, ta, tb);
+            if (grid.done) {
+                in_leaf = false;
+                done = tree.done;
             }
+            return hit;
         }
-        return hit;
+        float la, lb;
+        if (tree.step(a, r, tn, tf, la, lb)) {
+            grid.init(a, r, la);
+            leaf_tb = lb;
+            in_leaf = true;
+        }
+        done = tree.done && !in_leaf;
+        return false;
     }
 };
 
@@ -772,10 +776,11 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
         if (alive && walking) {
             float ta, tb;
             while (rg.n < RANGES && held < LOOKAHEAD) {
-                if (!w.next(a, r, tn, tf, ta, tb)) {
+                if (w.done) {
                     walking = false;
                     break;
                 }
+                if (!w.step(a, r, tn, tf, ta, tb)) continue;
                 float ka = ceilf((ta - tn) / a.dt) - 1.0f;
                 float kb = floorf((tb - tn) / a.dt) + 1.0f;
                 kb = kb < 16777216.0f ? kb : 16777216.0f;
