@@ -17,6 +17,9 @@
 // The device code lives in render_kernels.h; this file instantiates the plain
 // kernels and render_shaded.cu the shaded ones (gradient shading, R13, and
 // opacity correction, R14: the second render workload).
+#include <algorithm>
+#include <cmath>
+
 #include "render_kernels.h"
 
 namespace ess {
@@ -31,6 +34,10 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.value_lo = j.vol->value_lo;
     a.s = (float)(j.tf->nt - 1) / (j.vol->value_hi - j.vol->value_lo);
     a.cell_last = (uint32_t)((size_t)(j.vol->nx + 1) * (j.vol->ny + 1) * (j.vol->nz + 1) - 1);
+    a.cs_y = (uint32_t)(j.vol->nx + 1);
+    a.cs_z = (uint32_t)((j.vol->nx + 1) * (j.vol->ny + 1));
+    a.c_base = a.cs_z + a.cs_y + 1;
+    a.c_base_m = a.c_base - 0x4b400000u * (a.cs_z + a.cs_y + 1u);
     a.tf = j.tf->lut;
     a.nt = j.tf->nt;
     for (int i = 0; i < 3; ++i) {
@@ -51,6 +58,22 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.gx = j.st->gx;
     a.gy = j.st->gy;
     a.gz = j.st->gz;
+    {
+        // largest ray parameter of a sample: the farthest volume corner from
+        // the eye, plus the image plane's extent (orthographic origins)
+        double tmax = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            const double cx = (k & 1) ? j.vol->nx : 0, cy = (k & 2) ? j.vol->ny : 0,
+                         cz = (k & 4) ? j.vol->nz : 0;
+            const double dx = cx - j.cam.eye[0], dy = cy - j.cam.eye[1], dz = cz - j.cam.eye[2];
+            tmax = std::max(tmax, std::sqrt(dx * dx + dy * dy + dz * dz));
+        }
+        double ext = 0.0;
+        for (int i = 0; i < 3; ++i) ext += std::fabs(j.cam.u[i]) + std::fabs(j.cam.v[i]);
+        tmax += ext;
+        const double steps = (double)a.gx + a.gy + a.gz + 4.0;
+        a.dda_inc = steps * tmax * std::ldexp(1.0, -24) <= 0.25 * j.rp.dt ? 1 : 0;
+    }
     a.nodes = j.st->nodes;
     a.root = j.st->root;
     a.count = (j.st->kind == ESS_KD || j.st->kind == ESS_HYBRID) ? j.st->kd_count_dev : j.st->count;

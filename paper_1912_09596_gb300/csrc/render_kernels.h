@@ -14,6 +14,11 @@ struct RArgs {
     const void *cells;   // corner-replicated cells (nullptr: dense sampling only)
     int nx, ny, nz;
     uint32_t cell_last;  // index of the last cell ((nx+1)(ny+1)(nz+1) - 1 < 2^32)
+    // cell strides (y: nx+1, z: (nx+1)(ny+1)) and the index of cell (1, 1, 1),
+    // so that the cell of voxel (ix, iy, iz) is iz cs_z + iy cs_y + ix + c_base
+    uint32_t cs_y, cs_z, c_base;
+    uint32_t c_base_m;  // c_base - 0x4b400000 (cs_z + cs_y + 1), modulo 2^32
+    int dda_inc;        // host side: the grid may advance its crossings (GridWalkT<true>)
     float value_lo, s;   // TF coordinate x = (v - value_lo) * s
     const float4 *tf;    // 2 nt entries: entry i, then entry i+1 minus entry i
     int nt;
@@ -181,7 +186,7 @@ __device__ __forceinline__ uint32_t cell_index(const RArgs &a, int ix, int iy, i
 // it.
 __device__ __forceinline__ uint32_t cell_index_inside(const RArgs &a, int ix, int iy, int iz)
 {
-    const uint32_t i = (uint32_t)(((iz + 1) * (a.ny + 1) + (iy + 1)) * (a.nx + 1) + (ix + 1));
+    const uint32_t i = (uint32_t)iz * a.cs_z + (uint32_t)iy * a.cs_y + (uint32_t)ix + a.c_base;
     return min(i, a.cell_last);
 }
 
@@ -196,6 +201,7 @@ template <typename T> struct CellRaw<T, 0> {
     {
         Corners<T, 0>::get(a, ix, iy, iz, v);
     }
+    __device__ __forceinline__ void load_index(const RArgs &, uint32_t) {}
     __device__ __forceinline__ void corners(const RArgs &, float out[8]) const
     {
 #pragma unroll
@@ -222,6 +228,10 @@ template <> struct CellRaw<uint8_t, 1> {
     {
         c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + cell_of<INSIDE>(a, ix, iy, iz));
     }
+    __device__ __forceinline__ void load_index(const RArgs &a, uint32_t i)
+    {
+        c = __ldg(reinterpret_cast<const uint2 *>(a.cells) + i);
+    }
     __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
     {
         // byte b under the exponent of 2^23 is the float 2^23 + b: exact
@@ -246,6 +256,10 @@ template <> struct CellRaw<uint16_t, 1> {
     __device__ __forceinline__ void load(const RArgs &a, int ix, int iy, int iz)
     {
         c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + cell_of<INSIDE>(a, ix, iy, iz));
+    }
+    __device__ __forceinline__ void load_index(const RArgs &a, uint32_t i)
+    {
+        c = __ldg(reinterpret_cast<const uint4 *>(a.cells) + i);
     }
     __device__ __forceinline__ void corners(const RArgs &, float v[8]) const
     {
@@ -272,6 +286,12 @@ template <> struct CellRaw<float, 1> {
     {
         const float4 *p = reinterpret_cast<const float4 *>(a.cells) +
                           2 * (size_t)cell_of<INSIDE>(a, ix, iy, iz);
+        c0 = __ldg(p);
+        c1 = __ldg(p + 1);
+    }
+    __device__ __forceinline__ void load_index(const RArgs &a, uint32_t i)
+    {
+        const float4 *p = reinterpret_cast<const float4 *>(a.cells) + 2 * (size_t)i;
         c0 = __ldg(p);
         c1 = __ldg(p + 1);
     }
@@ -304,6 +324,21 @@ template <typename T, int SAMPLER> struct SampleFetch {
     __device__ __forceinline__ void at(const RArgs &a, float px, float py, float pz)
     {
         const float qx = px - 0.5f, qy = py - 0.5f, qz = pz - 0.5f;
+        if (INSIDE && SAMPLER == 1) {
+            // floor by adding 1.5 * 2^23 rounded down: |q| < 2^22, so the sum
+            // lies in [2^23, 2^24), where floats are the integers, and its
+            // bits are 0x4b400000 + floor(q)
+            const float M = 12582912.0f;
+            const float sx = __fadd_rd(qx, M), sy = __fadd_rd(qy, M), sz = __fadd_rd(qz, M);
+            fx = qx - (sx - M);
+            fy = qy - (sy - M);
+            fz = qz - (sz - M);
+            const uint32_t i = (uint32_t)__float_as_int(sz) * a.cs_z +
+                               (uint32_t)__float_as_int(sy) * a.cs_y +
+                               (uint32_t)__float_as_int(sx) + a.c_base_m;
+            raw.load_index(a, min(i, a.cell_last));
+            return;
+        }
         const float gxf = floorf(qx), gyf = floorf(qy), gzf = floorf(qz);
         fx = qx - gxf;
         fy = qy - gyf;
@@ -502,10 +537,14 @@ __device__ __forceinline__ void dda_axis(float o, float d, float inv, bool zero,
 // cell yields the span between its entry and exit crossing.  (A crossing
 // rounded to the wrong side of a corner only moves a sample whose cell is in
 // doubt, and such a sample is within half a voxel of both cells, so its
-// opacity is zero unless both are non-empty.)  Crossings are recomputed from
-// integer plane positions (no drift) and every axis only moves one way, so at
-// most gx+gy+gz steps.
-struct GridWalk {
+// opacity is zero unless both are non-empty.)  Every axis only moves one way,
+// so at most gx+gy+gz steps.  A crossing is recomputed from its integer plane
+// position, or, with INC (the kernel the host picks when the drift cannot
+// reach a quarter of the sample step: (steps + 4) t_max 2^-24 <= dt / 4, every
+// addition rounding by at most half an ulp of t_max), advanced by B |1/d|:
+// rule S takes one sample beyond each end of an interval, so a crossing off by
+// less than dt still covers every sample of a non-empty cell.
+template <bool INC> struct GridWalkT {
     int cx, cy, cz, sx, sy, sz, left;
     float tx, ty, tz, tcur;
     bool done;
@@ -541,20 +580,25 @@ struct GridWalk {
         if (tx <= ty && tx <= tz) {
             cx += sx;
             if (cx < 0 || cx >= a.gx) done = true;
-            tx = ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
+            tx = INC ? fmaf((float)B, fabsf(r.inv[0]), tx)
+                      : ((float)((cx + (sx > 0 ? 1 : 0)) * B) - r.o[0]) * r.inv[0];
         } else if (ty <= tz) {
             cy += sy;
             if (cy < 0 || cy >= a.gy) done = true;
-            ty = ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
+            ty = INC ? fmaf((float)B, fabsf(r.inv[1]), ty)
+                      : ((float)((cy + (sy > 0 ? 1 : 0)) * B) - r.o[1]) * r.inv[1];
         } else {
             cz += sz;
             if (cz < 0 || cz >= a.gz) done = true;
-            tz = ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
+            tz = INC ? fmaf((float)B, fabsf(r.inv[2]), tz)
+                      : ((float)((cz + (sz > 0 ? 1 : 0)) * B) - r.o[2]) * r.inv[2];
         }
         tcur = texit;
         return hit;
     }
 };
+
+using GridWalk = GridWalkT<false>;
 
 // Ordered traversal of a binary box tree.  Each inner node carries both
 // children's boxes (floats, voxel units); both are slab-tested, the child
@@ -831,6 +875,10 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
 }
 
 // ------------------------------------------------------------------ kernels
+// The grid walk with advanced crossings (GridWalkT<true>): a kernel variant,
+// not a structure kind of the interface.
+constexpr int KIND_GRID_INC = 8;
+
 // One pixel: ray, volume interval, traversal of the structure, background.
 // Shared by the plain and the batched kernels, so both give the same bits.
 template <typename T, int SAMPLER, int KIND, int SHADE>
@@ -847,8 +895,8 @@ __device__ __forceinline__ void render_pixel(const RArgs &a, int x, int y, long 
     if (tn < tf) {
         if (KIND == ESS_NONE) {
             trace_naive<T, SAMPLER, SHADE>(a, r, tn, tf, acc, ns);
-        } else if (KIND == ESS_GRID) {
-            GridWalk w;
+        } else if (KIND == ESS_GRID || KIND == KIND_GRID_INC) {
+            GridWalkT<KIND == KIND_GRID_INC> w;
             w.init(a, r, tn);
             trace_walk<T, SAMPLER, SHADE>(a, r, tn, tf, w, acc, ns);
         } else if (KIND == ESS_HYBRID) {
@@ -956,6 +1004,14 @@ template <int KIND, int SHADE> static void launch_kind(Ctx &c, const RArgs &a, e
 {
     dim3 grid((a.W + 2 * tw - 1) / (2 * tw), (a.H + 64 / tw - 1) / (64 / tw));
     bool cells = a.cells != nullptr;
+    if constexpr (KIND == KIND_GRID_INC) {  // cell samplers only
+        switch (dt) {
+        case ESS_U8: k_render<uint8_t, 1, KIND, SHADE><<<grid, 128, 0, c.stream>>>(a, tw); break;
+        case ESS_U16: k_render<uint16_t, 1, KIND, SHADE><<<grid, 128, 0, c.stream>>>(a, tw); break;
+        default: k_render<float, 1, KIND, SHADE><<<grid, 128, 0, c.stream>>>(a, tw); break;
+        }
+        return;
+    }
     switch (dt) {
     case ESS_U8:
         if (cells) k_render<uint8_t, 1, KIND, SHADE><<<grid, 128, 0, c.stream>>>(a, tw);
@@ -976,7 +1032,10 @@ template <int SHADE> void launch_render_kernels(Ctx &c, const RArgs &a, int kind
 {
     switch (kind) {
     case ESS_NONE: launch_kind<ESS_NONE, SHADE>(c, a, dt, tw); break;
-    case ESS_GRID: launch_kind<ESS_GRID, SHADE>(c, a, dt, tw); break;
+    case ESS_GRID:
+        if (a.dda_inc && a.cells != nullptr) launch_kind<KIND_GRID_INC, SHADE>(c, a, dt, tw);
+        else launch_kind<ESS_GRID, SHADE>(c, a, dt, tw);
+        break;
     case ESS_LBVH: launch_kind<ESS_LBVH, SHADE>(c, a, dt, tw); break;
     case ESS_HYBRID: launch_kind<ESS_HYBRID, SHADE>(c, a, dt, tw); break;
     default: launch_kind<ESS_KD, SHADE>(c, a, dt, tw); break;

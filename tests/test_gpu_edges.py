@@ -104,3 +104,35 @@ def test_smallest_and_largest_bricks(gpu, ctx, ora, B):
     ref, _ = ora.render_naive(ov, ot, cam, 48, 40, dt=0.5, ert=0.99, bg=(0.1, 0.2, 0.3, 0.4))
     for k, st in sts.items():
         assert_image_parity(_render(ess, torch, ctx, st, cam, 48, 40), ref, "B=%d %s" % (B, k))
+
+
+@pytest.mark.parametrize("dist,fov", [(1.6, 40.0), (1400.0, 0.08)])
+def test_grid_crossings_near_and_far_camera(gpu, ctx, ora, dist, fov):
+    """The grid walk advances its crossings by B |1/d| when the host bounds
+    their drift below dt / 4, and recomputes them from plane positions
+    otherwise: a camera 58,000 voxels away takes the second path.  Images
+    against the oracle's naive march, sample counts against its enumeration
+    of the non-empty bricks."""
+    ess, torch = gpu
+    v = synth.blobs_u8((48, 44, 52), n_blobs=7, seed=12)
+    tf = synth.tf_ramp(256, 50)
+    vol, t = upload(ess, torch, ctx, v, 0, 255, tf)
+    ov, ot = ora.OVolume(v, 0, 255), ora.OTF(tf)
+    W, H, B = 40, 36, 4
+    cam = synth.orbit_camera(v.shape[::-1], W, H, theta=0.9, phi=0.3, dist=dist, fov_deg=fov)
+    assert np.abs(cam.eye).max() < 60000.0
+    ref, _ = ora.render_naive(ov, ot, cam, W, H, dt=0.5, ert=2.0, bg=(0.1, 0.2, 0.3, 0.4))
+    mask = ora.build_mask(ov, ot, B)
+    boxes = ora.brick_boxes(np.nonzero(mask)[0], ov.grid(B), B, ov.dims)
+    _, n_ref = ora.render_boxes(ov, ot, cam, W, H, boxes, dt=0.5, ert=2.0)
+    assert n_ref > 10000
+    for k in ("GRID", "HYBRID"):
+        st = ess.ess_build(ctx, vol, t, getattr(ess, k),
+                           ess.build_params(brick=B, halting=0 if k == "HYBRID" else 1))
+        ess.ess_sample_count(ctx, reset=True)
+        img = _render(ess, torch, ctx, st, cam, W, H, ert=2.0)
+        n_gpu = ess.ess_sample_count(ctx, reset=True)
+        assert_image_parity(img, ref, "dist %g %s" % (dist, k))
+        if k == "GRID":
+            assert abs(n_gpu - n_ref) <= max(8, 0.002 * n_ref), (dist, n_gpu, n_ref)
+        ess.ess_release(ctx, st)
