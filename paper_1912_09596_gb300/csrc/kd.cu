@@ -20,7 +20,10 @@
 // node turns slab boxes into the prefix/suffix unions that are the candidate
 // L and R boxes and picks the split, and one kernel numbers and emits the
 // children (each block after the split counts of the blocks before it) and,
-// in its last block to finish, moves the level state on.  With an even nbins the middle plane lo + floor(e/2) is
+// in its last block to finish, moves the level state on.  For 4 bins the
+// decide and emit steps are one kernel, and the whole level loop runs either
+// as one cooperative launch with grid barriers between the steps (the
+// default), as a CUDA graph with a conditional while node, or from the host.  With an even nbins the middle plane lo + floor(e/2) is
 // candidate j = nbins/2, so a forced middle split also falls on a slab border.
 #include <cuda_runtime.h>
 
@@ -110,15 +113,25 @@ __device__ __forceinline__ void brick_coords(uint32_t b, int gx, int gy, int c[3
 // (brick coordinates are below 65536).
 constexpr int32_t KD_LO_BIAS = 65536;
 
-// Decodes a stored slab into a box; returns false for an empty slab.
-__device__ __forceinline__ bool slab_load(const int32_t *e, int32_t box[6])
+// Loads of words that other blocks of a running kernel write (the
+// persistent build): from L2 (ld.global.cg), never from a stale L1 line.
+template <bool CG> __device__ __forceinline__ int32_t kd_ld(const int32_t *p)
 {
+    return CG ? __ldcg(p) : *p;
+}
+
+// Decodes a stored slab into a box; returns false for an empty slab.
+template <bool CG = false> __device__ __forceinline__ bool slab_load(const int32_t *e, int32_t box[6])
+{
+    int32_t w[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = kd_ld<CG>(e + k);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        box[k] = KD_LO_BIAS - e[k];
-        box[3 + k] = e[3 + k];
+        box[k] = KD_LO_BIAS - w[k];
+        box[3 + k] = w[3 + k];
     }
-    return e[0] != 0;
+    return w[0] != 0;
 }
 
 // Level state, in device memory so that the level loop can run without the
@@ -131,7 +144,7 @@ struct KdState {
     int splits;      // splits on the current level
     unsigned done;   // emit blocks finished on the current level
     unsigned epoch;  // bumped by every build: tags the look-back words of its levels
-    int pad;
+    unsigned bar;    // arrivals at the grid barriers of the persistent build
 };
 
 // Slab buffer of the current level (parity of the level number) and of the next.
@@ -157,6 +170,7 @@ __global__ void k_kd_root_init(int32_t *root_box, KdState *st)
         st->splits = 0;
         st->done = 0;
         st->epoch += 1;
+        st->bar = 0;
     }
 }
 
@@ -213,33 +227,34 @@ __global__ void k_kd_init(const int *__restrict__ count, const int32_t *__restri
 // in shared memory takes the min/max, and each block then applies one set of
 // global atomics per distinct slab (min/max are order independent, so the
 // result is the same as with direct atomics).
-constexpr int KD_HT = 128;  // shared hash slots per block
+constexpr int KD_HT = 128;          // shared hash slots per block of the per-level kernel
+constexpr int KD_HT_PERSIST = 1024;  // ... of the persistent build (one block per SM)
 
 __device__ __forceinline__ void slab_atomic(int32_t *slot, const int v[6])
 {
     for (int k = 0; k < 6; ++k) atomicMax(slot + k, v[k]);
 }
 
+// One level of the accumulate step over the bricks this block takes (a
+// grid-stride loop), through the shared hash table s_key / s_val of HT slots.
 // NBINS > 0: the bin count known at compile time (divisions become shifts).
-template <int NBINS>
-__global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restrict__ ids,
-                                                       const int *__restrict__ count,
-                                                       int *__restrict__ brick_node,
-                                                       const int32_t *__restrict__ nodes9,
-                                                       int32_t *slabs0, int32_t *slabs1,
-                                                       const KdState *st, KdParams P)
+// CG: node records are read from L2 (the persistent build, where other blocks
+// wrote them during the same kernel).
+template <int NBINS, bool CG, int HT>
+__device__ __forceinline__ void kd_accumulate_level(const uint32_t *__restrict__ ids, int n,
+                                                    int *__restrict__ brick_node,
+                                                    const int32_t *nodes9, int32_t *slabs,
+                                                    int prev_begin, int lvl_begin, int lvl_size,
+                                                    const KdParams &P, long long *s_key,
+                                                    int (*s_val)[6])
 {
-    __shared__ long long s_key[KD_HT];
-    __shared__ int s_val[KD_HT][6];
-    const int prev_begin = st->prev_begin, lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
-    if (lvl_size <= 0) return;  // uniform
-    int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
-    for (int h = threadIdx.x; h < KD_HT; h += blockDim.x) {
+    constexpr int HB = HT == 1024 ? 10 : HT == 512 ? 9 : HT == 256 ? 8 : 7;
+    static_assert(HT == (1 << HB), "hash table size: a power of two, 128 to 1024");
+    for (int h = threadIdx.x; h < HT; h += blockDim.x) {
         s_key[h] = -1;
         for (int k = 0; k < 6; ++k) s_val[h][k] = 0;
     }
     __syncthreads();
-    const int n = *count;
     for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const int i = base + threadIdx.x;  // the loop is uniform per block
         bool live = i < n;
@@ -250,9 +265,9 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
             node = lvl_begin == 0 ? 0 : brick_node[i];
             if (node >= prev_begin && node < lvl_begin) {
                 const int32_t *rec = nodes9 + 9 * (size_t)node;
-                int fc = rec[8];
+                int fc = kd_ld<CG>(rec + 8);
                 if (fc >= 0) {
-                    node = fc + (c[rec[6]] >= rec[7] ? 1 : 0);
+                    node = fc + (c[kd_ld<CG>(rec + 6)] >= kd_ld<CG>(rec + 7) ? 1 : 0);
                     brick_node[i] = node;
                 }
             } else if (lvl_begin == 0) {
@@ -260,7 +275,10 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
             }
             if (node < lvl_begin || node >= lvl_begin + lvl_size) live = false;
         }
-        const int32_t *box = nodes9 + 9 * (size_t)(live ? node : 0);
+        const int32_t *bp = nodes9 + 9 * (size_t)(live ? node : 0);
+        int32_t box[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) box[k] = kd_ld<CG>(bp + k);
         int local = node - lvl_begin;
         const int v[6] = {KD_LO_BIAS - c[0], KD_LO_BIAS - c[1], KD_LO_BIAS - c[2],
                           c[0] + 1, c[1] + 1, c[2] + 1};
@@ -277,9 +295,9 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
                 for (int k = 0; k < 6; ++k) r[k] = __reduce_max_sync(0xffffffffu, v[k]);
                 if ((threadIdx.x & 31) == 0) slab_atomic(slabs + 6 * first, r);
             } else if (use) {
-                int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> 57);  // 7 bits
+                int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> (64 - HB));
                 bool done = false;
-                for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (KD_HT - 1)) {
+                for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (HT - 1)) {
                     long long old = atomicCAS((unsigned long long *)&s_key[h], (unsigned long long)-1ll,
                                               (unsigned long long)slot_id);
                     if (old == -1 || old == slot_id) {
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
         }
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < KD_HT; h += blockDim.x) {
+    for (int h = threadIdx.x; h < HT; h += blockDim.x) {
         long long key = s_key[h];
         if (key >= 0) {
             int r[6];
@@ -300,6 +318,23 @@ __global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restric
             slab_atomic(slabs + 6 * key, r);
         }
     }
+}
+
+template <int NBINS>
+__global__ void __launch_bounds__(256) k_kd_accumulate(const uint32_t *__restrict__ ids,
+                                                       const int *__restrict__ count,
+                                                       int *__restrict__ brick_node,
+                                                       const int32_t *__restrict__ nodes9,
+                                                       int32_t *slabs0, int32_t *slabs1,
+                                                       const KdState *st, KdParams P)
+{
+    __shared__ long long s_key[KD_HT];
+    __shared__ int s_val[KD_HT][6];
+    const int prev_begin = st->prev_begin, lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if (lvl_size <= 0) return;  // uniform
+    kd_accumulate_level<NBINS, false, KD_HT>(ids, *count, brick_node, nodes9,
+                                             kd_cur_slabs(slabs0, slabs1, st), prev_begin,
+                                             lvl_begin, lvl_size, P, s_key, s_val);
 }
 
 __device__ __forceinline__ void box_union(int32_t *acc, const int32_t *s)
@@ -460,44 +495,48 @@ constexpr unsigned long long KD_LB_AGG = 1ull << 30, KD_LB_INC = 2ull << 30;
 constexpr unsigned long long KD_LB_MASK = (1ull << 30) - 1;
 constexpr long KD_LB_SPIN_LIMIT = 1l << 24;
 
-__global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_t *slabs0,
-                                                         int32_t *slabs1,
-                                                         unsigned long long *chunk_st, KdState *st,
-                                                         KdParams P, int next_cap, int capacity,
-                                                         int max_levels, uint32_t *status,
-                                                         cudaGraphConditionalHandle handle,
-                                                         int use_handle)
+// One level of the fused 4-bin decide and emit over the chunks of CH nodes
+// (16 lanes per node) this block takes: zeroes the next level's slab region,
+// decides every node of the level, numbers the children through the
+// look-back words (tagged with `tag`) and writes the split nodes' records and
+// their children.  The last chunk stores the level's split count in *splits.
+// CG: node records and slabs are read from L2 (the persistent build).
+template <bool CG, int CH>
+__device__ __forceinline__ void kd_decide_emit4_level(int32_t *nodes9, const int32_t *slabs,
+                                                      int32_t *next_slabs,
+                                                      unsigned long long *chunk_st, int *splits,
+                                                      const KdParams &P, int next_cap,
+                                                      int capacity, uint32_t *status,
+                                                      int lvl_begin, int lvl_size,
+                                                      unsigned long long tag)
 {
     constexpr int S = 4;
-    const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
-    if (lvl_size <= 0) {  // uniform: the tree is done
-        if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0u);
-        return;
-    }
-    const unsigned long long tag = ((unsigned long long)((st->epoch << 8) | (unsigned)st->levels)) << 32;
+    static_assert(CH <= 32, "one ballot covers a chunk's nodes");
     {
         // the next level has at most min(2 lvl_size, capacity) nodes
-        int2 *next = reinterpret_cast<int2 *>(kd_next_slabs(slabs0, slabs1, st));
+        int2 *next = reinterpret_cast<int2 *>(next_slabs);
         const size_t words = (size_t)min(2 * lvl_size, next_cap) * 9 * S;  // 18 S ints per node
         const size_t stride = (size_t)gridDim.x * blockDim.x;
         for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < words; q += stride)
             next[q] = make_int2(0, 0);
     }
-    const int32_t *slabs = kd_cur_slabs(slabs0, slabs1, st);
-    const unsigned long long Vroot = kd_volume(nodes9, P);
+    int32_t root[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) root[k] = kd_ld<CG>(nodes9 + k);
+    const unsigned long long Vroot = kd_volume(root, P);
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const int a = (hl >> 2) < 3 ? hl >> 2 : 0, j = hl & 3;
     const bool slab_lane = hl < 12;
-    __shared__ KdDecision sdec[KD_CHUNK];
+    __shared__ KdDecision sdec[CH];
     __shared__ int s_excl;
-    const int nchunks = (lvl_size + KD_CHUNK - 1) / KD_CHUNK;
+    const int nchunks = (lvl_size + CH - 1) / CH;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {  // uniform per block
-        const int l = ch * KD_CHUNK + 2 * (threadIdx.x >> 5) + half;
+        const int l = ch * CH + 2 * (threadIdx.x >> 5) + half;
         const bool node = l < lvl_size;
         const int32_t *X = nodes9 + 9 * (size_t)(lvl_begin + (node ? l : 0));
         int32_t x[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) x[k] = X[k];
+        for (int k = 0; k < 6; ++k) x[k] = kd_ld<CG>(X + k);
         const unsigned long long V = kd_volume(x, P);
         const bool allowed = node && (P.halting == 0 ? (10ull * V > Vroot) : (V > 512ull));
         const int lo = x[a], hi = x[3 + a];
@@ -506,7 +545,7 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
         int32_t b[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
         if (allowed && axis_ok && j < ns) {
             int32_t t[6];
-            if (slab_load(slabs + 6 * (((size_t)l * 3 + a) * S + j), t)) {
+            if (slab_load<CG>(slabs + 6 * (((size_t)l * 3 + a) * S + j), t)) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) b[k] = t[k];
             }
@@ -591,12 +630,12 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
                     d.R[k] = dr[k];
                 }
             }
-            sdec[l - ch * KD_CHUNK] = d;
+            sdec[l - ch * CH] = d;
         }
         __syncthreads();
         // the chunk's split count, chained to the chunks before it
         if (threadIdx.x < 32) {
-            const unsigned ball = __ballot_sync(0xffffffffu, lane < KD_CHUNK && sdec[lane].split);
+            const unsigned ball = __ballot_sync(0xffffffffu, lane < CH && sdec[lane].split);
             if (lane == 0) {
                 const unsigned long long cnt = (unsigned long long)__popc(ball);
                 volatile unsigned long long *cs = chunk_st;
@@ -621,12 +660,12 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
                 __threadfence();
                 cs[ch] = tag | KD_LB_INC | (excl + cnt);
                 s_excl = (int)excl;
-                if (ch == nchunks - 1) st->splits = (int)(excl + cnt);
+                if (ch == nchunks - 1) *splits = (int)(excl + cnt);
             }
         }
         __syncthreads();
         // emit: children of the chunk's split nodes, numbered in node order
-        if (threadIdx.x < KD_CHUNK && sdec[threadIdx.x].split) {
+        if (threadIdx.x < CH && sdec[threadIdx.x].split) {
             int rank = 0;
             for (int k = 0; k < (int)threadIdx.x; ++k) rank += sdec[k].split;
             const int fc = lvl_begin + lvl_size + 2 * (s_excl + rank);
@@ -634,7 +673,7 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
                 atomicOr(status, DEV_ERR_OVERFLOW);
             } else {
                 const KdDecision &d = sdec[threadIdx.x];
-                int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + ch * KD_CHUNK + threadIdx.x);
+                int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + ch * CH + threadIdx.x);
                 rec[6] = d.axis;
                 rec[7] = d.plane;
                 rec[8] = fc;
@@ -651,6 +690,26 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
         }
         __syncthreads();  // sdec and s_excl are rewritten by the next chunk
     }
+}
+
+__global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_t *slabs0,
+                                                         int32_t *slabs1,
+                                                         unsigned long long *chunk_st, KdState *st,
+                                                         KdParams P, int next_cap, int capacity,
+                                                         int max_levels, uint32_t *status,
+                                                         cudaGraphConditionalHandle handle,
+                                                         int use_handle)
+{
+    const int lvl_begin = st->lvl_begin, lvl_size = st->lvl_size;
+    if (lvl_size <= 0) {  // uniform: the tree is done
+        if (use_handle && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0u);
+        return;
+    }
+    const unsigned long long tag = ((unsigned long long)((st->epoch << 8) | (unsigned)st->levels)) << 32;
+    kd_decide_emit4_level<false, KD_CHUNK>(nodes9, kd_cur_slabs(slabs0, slabs1, st),
+                                           kd_next_slabs(slabs0, slabs1, st), chunk_st,
+                                           &st->splits, P, next_cap, capacity, status, lvl_begin,
+                                           lvl_size, tag);
     // the last block to finish advances the level
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -672,6 +731,90 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
     st->lvl_size = next;
     st->splits = 0;
     if (use_handle) cudaGraphSetConditional(handle, next > 0 ? 1u : 0u);
+}
+
+// ---------------------------------------------------- persistent 4-bin build
+// The whole level loop of a 4-bin build in one cooperative launch (all blocks
+// resident, one per SM): per level the accumulate step, a grid barrier, the
+// fused decide and emit step, a grid barrier; every block then advances its
+// own copy of the level state from the level's split count.  The same level
+// bodies as the per-level kernels, so the same tree.
+
+// Grid barrier on a monotone arrival counter: the k-th barrier of a launch
+// completes when the counter reaches k x gridDim.x.  The wait is bounded; a
+// block that gives up sets DEV_ERR_TIMEOUT and returns false (the caller
+// leaves the kernel; the other blocks then give up at their next barrier).
+constexpr long KD_BAR_SPIN_LIMIT = 1l << 22;  // polls of L2, a few seconds at most
+// Threads per block, 16 per node of a decide chunk (512, with 32-node chunks,
+// measured slower).
+constexpr int KD_PERSIST_THREADS = 256;
+
+__device__ __forceinline__ bool kd_grid_sync(unsigned *bar, unsigned target, uint32_t *status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        long spins = 0;
+        while (*(volatile unsigned *)bar < target) {
+            if (++spins > KD_BAR_SPIN_LIMIT) {
+                atomicOr(status, DEV_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(KD_PERSIST_THREADS) k_kd_build4(
+    const uint32_t *__restrict__ ids, const int *__restrict__ count, int *__restrict__ brick_node,
+    int32_t *nodes9, int32_t *slabs0, int32_t *slabs1, unsigned long long *chunk_st, KdState *st,
+    KdParams P, int next_cap, int capacity, int max_levels, uint32_t *status)
+{
+    __shared__ long long s_key[KD_HT_PERSIST];
+    __shared__ int s_val[KD_HT_PERSIST][6];
+    int lvl_size = st->lvl_size;  // 1, or 0 for an empty mask (k_kd_init)
+    if (lvl_size <= 0) return;    // uniform
+    const unsigned epoch = st->epoch;
+    const int n = *count;
+    int prev_begin = 0, lvl_begin = 0, levels = 0;
+    unsigned target = 0;
+    while (true) {
+        int32_t *cur = (levels & 1) ? slabs1 : slabs0, *nxt = (levels & 1) ? slabs0 : slabs1;
+        kd_accumulate_level<4, true, KD_HT_PERSIST>(ids, n, brick_node, nodes9, cur, prev_begin,
+                                                    lvl_begin, lvl_size, P, s_key, s_val);
+        if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
+        const unsigned long long tag = ((unsigned long long)((epoch << 8) | (unsigned)levels)) << 32;
+        kd_decide_emit4_level<true, KD_PERSIST_THREADS / 16>(nodes9, cur, nxt, chunk_st,
+                                                             &st->splits, P, next_cap, capacity,
+                                                             status, lvl_begin, lvl_size, tag);
+        if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
+        // st->splits is rewritten only after the next level's first barrier
+        int next = 2 * *(volatile int *)&st->splits;
+        prev_begin = lvl_begin;
+        lvl_begin += lvl_size;
+        levels += 1;
+        if (next > 0 && (lvl_begin + next > capacity || levels >= max_levels)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, DEV_ERR_OVERFLOW);
+            next = 0;
+        }
+        lvl_size = next;
+        if (lvl_size == 0) break;  // uniform
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->prev_begin = prev_begin;
+        st->lvl_begin = lvl_begin;
+        st->lvl_size = 0;
+        st->levels = levels;
+        st->splits = 0;
+        st->done = 0;
+    }
 }
 
 // Sum of v over the block (256 threads).
@@ -957,7 +1100,8 @@ static bool kd_graph_fits(const Structure &s, int S)
 // condition.
 constexpr int KD_LEVELS_PER_ITERATION = 4;
 
-static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
+// Level buffers for the widest possible level (one node per non-empty brick).
+static void kd_full_buffers(Ctx &c, Structure &s, const KdParams &P)
 {
     size_t cap = (size_t)s.nb;
     size_t slab_words = (size_t)3 * P.S * 6;
@@ -974,6 +1118,53 @@ static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
     grow(c, bs, s.kd_bs_cap, (cap + 255) / 256, sizeof(uint32_t));
     s.kd_block_sums = (uint32_t *)bs;
     kd_chunk_reserve(c, s);
+}
+
+// Blocks of the persistent 4-bin build: one per SM when the device launches
+// cooperative kernels and fits one block per SM, else 0 (not available).  Two
+// or four per SM measured slower (the grid barriers cost more).  The
+// environment variable ESS_KD_PERSIST=0 turns it off (the graph runs instead).
+static int kd_persist_blocks(Ctx &c)
+{
+    const char *env = std::getenv("ESS_KD_PERSIST");
+    if (env && env[0] == '0') return 0;
+    int coop = 0, sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c.device) != cudaSuccess || !coop)
+        return 0;
+    ESS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    ESS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_kd_build4,
+                                                           KD_PERSIST_THREADS, 0));
+    return per_sm >= 1 ? sms : 0;
+}
+
+// Root kernels, the cooperative level loop and the traversal layout.
+static void kd_build_persistent(Ctx &c, Structure &s, const KdParams &P, int blocks)
+{
+    kd_full_buffers(c, s, P);
+    const size_t cap = (size_t)s.nb;
+    KdState *st = (KdState *)s.kd_state;
+    kd_root_launches(c, s, P, (unsigned)((cap + 255) / 256));
+    int next_cap = (int)std::min(s.kd_slab_cap[0], s.kd_slab_cap[1]);
+    int capacity = s.kd_capacity, max_levels = KD_MAX_LEVELS;
+    KdParams Pk = P;
+    const uint32_t *ids = s.ids;
+    const int *count = s.count;
+    int *brick_node = s.brick_node;
+    int32_t *nodes9 = s.kd_nodes, *s0 = s.kd_slabs[0], *s1 = s.kd_slabs[1];
+    unsigned long long *chunk = s.kd_chunk;
+    uint32_t *status = c.dev_status;
+    void *args[] = {&ids, &count, &brick_node, &nodes9, &s0, &s1, &chunk, &st,
+                    &Pk, &next_cap, &capacity, &max_levels, &status};
+    ESS_CUDA(cudaLaunchCooperativeKernel((const void *)k_kd_build4, dim3((unsigned)blocks),
+                                         dim3(KD_PERSIST_THREADS), args, 0, c.stream));
+    k_kd_pack<<<(unsigned)((2 * cap + 255) / 256), 256, 0, c.stream>>>(
+        s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root, P.B);
+}
+
+static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
+{
+    size_t cap = (size_t)s.nb;
+    kd_full_buffers(c, s, P);
     if (!c.capture_stream)
         ESS_CUDA(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
 
@@ -1046,6 +1237,15 @@ void launch_kd(Ctx &c, Structure &s)
     KdParams P = kd_params(s);
     s.height = -1;
     s.kd_count = -1;
+    if (P.S == 4 && kd_graph_fits(s, P.S)) {
+        // device-driven: the whole level loop is one cooperative launch
+        const int blocks = kd_persist_blocks(c);
+        if (blocks > 0) {
+            Launch L(c, "kd_build");
+            kd_build_persistent(c, s, P, blocks);
+            return;
+        }
+    }
     if (s.kd_exec || kd_graph_fits(s, P.S)) {
         // device-driven: the whole level loop is one graph launch
         if (!s.kd_exec) kd_build_graph(c, s, P);

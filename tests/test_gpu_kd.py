@@ -56,16 +56,20 @@ def test_kd_nodes_bit_exact(gpu, ctx, ora, case, nbins, halting, mls, B):
 
 
 @pytest.mark.parametrize("case", CASES[:2], ids=lambda c: c[0])
-def test_kd_host_loop_equals_graph(gpu, ctx, ora, case, monkeypatch):
-    """ESS_KD_GRAPH=0 (the host-driven level loop that per-kernel profilers
-    need) builds the same tree as the device-driven graph, which itself
-    equals the oracle."""
+@pytest.mark.parametrize("env", [{"ESS_KD_GRAPH": "0"}, {"ESS_KD_PERSIST": "0"}, {}],
+                         ids=["host_loop", "graph", "persistent"])
+def test_kd_build_paths_equal_oracle(gpu, ctx, ora, case, env, monkeypatch):
+    """The three drivers of a 4-bin build give the oracle's tree: the
+    host-driven level loop (ESS_KD_GRAPH=0, the one per-kernel profilers
+    need), the CUDA graph with a conditional while node (ESS_KD_PERSIST=0)
+    and the default single cooperative launch."""
     name, vf, (lo, hi), tff = case
-    v, tf = vf(), tff()
-    monkeypatch.setenv("ESS_KD_GRAPH", "0")
-    check_kd(gpu, ctx, ora, v, lo, hi, tf, 8, 4, 1, 32)
-    monkeypatch.setenv("ESS_KD_GRAPH", "1")
-    check_kd(gpu, ctx, ora, v, lo, hi, tf, 8, 4, 1, 32)
+    for k in ("ESS_KD_GRAPH", "ESS_KD_PERSIST"):
+        monkeypatch.delenv(k, raising=False)
+    for k, val in env.items():
+        monkeypatch.setenv(k, val)
+    check_kd(gpu, ctx, ora, vf(), lo, hi, tff(), 8, 4, 1, 32)
+    check_kd(gpu, ctx, ora, vf(), lo, hi, tff(), 4, 4, 0, 0)
 
 
 def test_kd_menger_shallow_single_node(gpu, ctx, ora):
