@@ -485,9 +485,10 @@ __global__ void __launch_bounds__(256) k_kd_decide(const int32_t *__restrict__ n
 // The same kernel emits the children.  A block takes chunks of 16
 // consecutive nodes (one per half-warp) in increasing order; the split count
 // of chunk c is chained to the chunks before it by a decoupled look-back (one
-// 64-bit word per chunk: the level's tag, a flag and the count or prefix), so
-// the children of chunk c are numbered right after those of chunks < c, in
-// breadth-first order.  The last block to finish moves the level state on.
+// 64-bit word per chunk: the level's tag, a flag and the count or prefix; a
+// warp reads 32 predecessors' words per step), so the children of chunk c are
+// numbered right after those of chunks < c, in breadth-first order.  The last
+// block to finish moves the level state on.
 __device__ __forceinline__ bool box_nonempty(const int32_t *b) { return b[0] != INT_MAX; }
 
 constexpr int KD_CHUNK = 16;                    // nodes per look-back chunk
@@ -633,30 +634,40 @@ __device__ __forceinline__ void kd_decide_emit4_level(int32_t *nodes9, const int
             sdec[l - ch * CH] = d;
         }
         __syncthreads();
-        // the chunk's split count, chained to the chunks before it
+        // the chunk's split count, chained to the chunks before it: the first
+        // warp reads the words of 32 predecessors at a time (lane i: chunk
+        // base - i) and adds counts up to the nearest inclusive prefix
         if (threadIdx.x < 32) {
             const unsigned ball = __ballot_sync(0xffffffffu, lane < CH && sdec[lane].split);
-            if (lane == 0) {
-                const unsigned long long cnt = (unsigned long long)__popc(ball);
-                volatile unsigned long long *cs = chunk_st;
-                unsigned long long excl = 0;
-                if (ch > 0) {
-                    cs[ch] = tag | KD_LB_AGG | cnt;
-                    for (int j = ch - 1; j >= 0; --j) {
-                        unsigned long long v = 0;
+            const unsigned long long cnt = (unsigned long long)__popc(ball);
+            volatile unsigned long long *cs = chunk_st;
+            unsigned long long excl = 0;
+            if (ch > 0) {
+                if (lane == 0) cs[ch] = tag | KD_LB_AGG | cnt;
+                for (int base = ch - 1;; base -= 32) {
+                    const int jj = base - lane;
+                    unsigned long long v = KD_LB_INC;  // before chunk 0: an inclusive prefix of 0
+                    if (jj >= 0) {
                         long spins = 0;
-                        while (((v = cs[j]) & ~(KD_LB_MASK | KD_LB_AGG | KD_LB_INC)) != tag ||
+                        while (((v = cs[jj]) & ~(KD_LB_MASK | KD_LB_AGG | KD_LB_INC)) != tag ||
                                (v & (KD_LB_AGG | KD_LB_INC)) == 0ull) {
-                            if (++spins > KD_LB_SPIN_LIMIT) break;
+                            if (++spins > KD_LB_SPIN_LIMIT) {
+                                atomicOr(status, DEV_ERR_TIMEOUT);
+                                v = KD_LB_INC;
+                                break;
+                            }
                         }
-                        if (spins > KD_LB_SPIN_LIMIT) {
-                            atomicOr(status, DEV_ERR_TIMEOUT);
-                            break;
-                        }
-                        excl += v & KD_LB_MASK;
-                        if (v & KD_LB_INC) break;
                     }
+                    const unsigned inc = __ballot_sync(0xffffffffu, (v & KD_LB_INC) != 0ull);
+                    const int stop = inc ? __ffs(inc) - 1 : 31;  // the nearest inclusive prefix
+                    unsigned long long add = lane <= stop ? (v & KD_LB_MASK) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                    excl += add;
+                    if (inc) break;  // uniform
                 }
+            }
+            if (lane == 0) {
                 __threadfence();
                 cs[ch] = tag | KD_LB_INC | (excl + cnt);
                 s_excl = (int)excl;
