@@ -274,7 +274,7 @@ void free_structure(Ctx &c, Structure &s)
     join_build(c, s);
     void *ptrs[] = {s.mask, s.ids, s.count, s.block_sums, s.keys, s.keys_sorted, s.ids_sorted,
                     s.keys_alt, s.ids_alt, s.sort_scratch, s.left, s.right, s.parent,
-                    s.leaf_parent, s.inner_box, s.inner_cnt, s.arrive, s.nodes, s.root, s.kd_nodes,
+                    s.leaf_parent, s.inner_box, s.range_end, s.chunk_box, s.nodes, s.root, s.kd_nodes,
                     s.kd_count_dev, s.brick_node, s.kd_scratch_i32, s.kd_state};
     for (void *p : ptrs) c.free(p);
     kd_free(c, s);
@@ -305,8 +305,8 @@ void alloc_lbvh(Ctx &c, Structure &s)
     s.parent = alloc_n<int32_t>(c, s, inner);
     s.leaf_parent = alloc_n<int32_t>(c, s, cap);
     s.inner_box = alloc_n<int32_t>(c, s, 6 * inner);
-    s.inner_cnt = alloc_n<int32_t>(c, s, inner);
-    s.arrive = alloc_n<int>(c, s, inner);
+    s.range_end = alloc_n<int32_t>(c, s, inner);
+    s.chunk_box = alloc_n<int32_t>(c, s, 6 * lbvh_chunk_boxes(cap));
     s.nodes = alloc_n<BoxNode>(c, s, inner);
     s.root = alloc_n<int32_t>(c, s, 8);
 }

@@ -121,8 +121,8 @@ struct Structure {
     uint32_t *sort_scratch = nullptr;
     int32_t *left = nullptr, *right = nullptr, *parent = nullptr, *leaf_parent = nullptr;
     int32_t *inner_box = nullptr;  // (n-1) x 6
-    int32_t *inner_cnt = nullptr;  // (n-1): leaves under each inner node
-    int *arrive = nullptr;
+    int32_t *range_end = nullptr;  // (n-1): the far end of each inner node's leaf range
+    int32_t *chunk_box = nullptr;  // boxes of 32, 1024 and 32768 consecutive sorted leaves
     BoxNode *nodes = nullptr;      // traversal nodes (LBVH: n-1; k-d: inner nodes)
     int32_t *root = nullptr;       // device root record: ref, then the box as 6 floats (voxels)
     int height = 0;
@@ -266,6 +266,8 @@ void launch_compact(Ctx &c, const uint8_t *mask, int64_t nb, uint32_t *ids, int 
 
 // lbvh.cu
 size_t sort_scratch_words(int64_t cap);
+// Boxes in the LBVH's chunk tables for up to cap leaves (6 ints each).
+size_t lbvh_chunk_boxes(size_t cap);
 int launch_radix_sort(Ctx &c, const uint32_t *keys, const uint32_t *vals, uint32_t *keys_a,
                       uint32_t *vals_a, uint32_t *keys_b, uint32_t *vals_b, const int *count,
                       int64_t cap, int bits, uint32_t *scratch);

@@ -247,7 +247,8 @@ __device__ __forceinline__ int rs_delta(const uint32_t *k, int n, int i, int j)
 
 __global__ void k_karras(const uint32_t *__restrict__ k, const int *__restrict__ count,
                          int32_t *__restrict__ left, int32_t *__restrict__ right,
-                         int32_t *__restrict__ parent, int32_t *__restrict__ leaf_parent)
+                         int32_t *__restrict__ parent, int32_t *__restrict__ leaf_parent,
+                         int32_t *__restrict__ range_end)
 {
     int n = *count;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,17 +273,21 @@ __global__ void k_karras(const uint32_t *__restrict__ k, const int *__restrict__
     int rc = (hi == g + 1) ? -1 - (g + 1) : g + 1;
     left[i] = lc;
     right[i] = rc;
+    range_end[i] = j;
     if (lc >= 0) parent[lc] = i; else leaf_parent[g] = i;
     if (rc >= 0) parent[rc] = i; else leaf_parent[g + 1] = i;
     if (i == 0) parent[0] = -1;
 }
 
-// ------------------------------------------------------- K7 bottom-up boxes
-// One thread per leaf climbs towards the root; at each inner node the first
-// arriving thread stops and the second (whose sibling subtree is complete)
-// unions the two child boxes, writes the node's box and its traversal node,
-// and climbs on.  Writers fence before the arrival counter; readers load with
-// .cg so that they see boxes written on other SMs.
+// ------------------------------------------------------- K7 node boxes
+// An inner node covers a contiguous range of the sorted leaves, so its box is
+// the union of the leaf boxes in that range (the same values a bottom-up
+// union gives).  The leaves are cut into chunks of 32, 1024 and 32768; a
+// first pass stores every chunk's box, and each inner node then unions its
+// two children's ranges from at most 31 leaves, 31 + 31 chunks of 32, 31 +
+// 31 chunks of 1024 and the chunks of 32768 between them.  No step waits for
+// another node, unlike a bottom-up pass whose threads climb one level per
+// dependent atomic.
 //
 // Solid subtrees: an inner node whose leaf count equals the number of bricks
 // in its box covers that box with non-empty bricks and nothing else, so the
@@ -318,68 +323,157 @@ __device__ __forceinline__ void write_root(int32_t *root, int32_t ref, const int
     for (int a = 0; a < 6; ++a) root[1 + a] = __float_as_int((float)(box[a] * B));
 }
 
-__global__ void k_lbvh_bounds(const uint32_t *__restrict__ sorted_ids, const int *__restrict__ count,
-                              const int32_t *__restrict__ left, const int32_t *__restrict__ right,
-                              const int32_t *__restrict__ parent,
-                              const int32_t *__restrict__ leaf_parent, int *arrive,
-                              int32_t *inner_box, int32_t *inner_cnt, BoxNode *nodes,
-                              int32_t *root, int gx, int gy, int B)
+constexpr int32_t LB_BIAS = 65536;  // brick coordinates are below 2^16
+
+size_t lbvh_chunk_boxes(size_t cap)
 {
-    int n = *count;
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    int32_t box[6];
-    brick_box(sorted_ids[j], gx, gy, box);
-    if (n == 1) {
-        // a single non-empty brick: the root is that leaf
-        write_root(root, -1 - (int32_t)sorted_ids[0], box, B);
-        return;
+    return cap / 32 + cap / 1024 + cap / 32768 + 3;
+}
+
+__device__ __forceinline__ void box_empty(int32_t b[6])
+{
+    b[0] = b[1] = b[2] = INT_MAX;
+    b[3] = b[4] = b[5] = INT_MIN;
+}
+
+__device__ __forceinline__ void box_add(int32_t acc[6], const int32_t b[6])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = min(acc[a], b[a]);
+        acc[3 + a] = max(acc[3 + a], b[3 + a]);
     }
-    int p = leaf_parent[j];
-    // a valid tree has at most 31 levels; the bound only guards a corrupt one
-    for (int level = 0; p >= 0 && p < n - 1 && level < 64; ++level) {
-        __threadfence();
-        if (atomicAdd(arrive + p, 1) == 0) return;
-        __threadfence();
-        int32_t lb[6], rb[6];
-        int lc = __ldcg(left + p), rc = __ldcg(right + p);
-        int32_t lcnt = 1, rcnt = 1;
-        if (lc < 0) {
-            brick_box(__ldg(sorted_ids + (-1 - lc)), gx, gy, lb);
-        } else {
+}
+
+// Chunk boxes: one block of 1024 threads per chunk of 1024 sorted leaves.
+// Chunk-of-32 boxes from warp reductions, chunk-of-1024 boxes from the
+// block's warps, chunk-of-32768 boxes by integer atomics on (bias - lo, hi),
+// zeroed before the launch.  A single leaf makes the root itself.
+__global__ void __launch_bounds__(1024) k_lbvh_chunks(const uint32_t *__restrict__ sorted_ids,
+                                                      const int *__restrict__ count,
+                                                      int32_t *chunk_box, int32_t *root, int gx,
+                                                      int gy, int B, int64_t cap)
+{
+    const int n = *count;
+    const int j = blockIdx.x * 1024 + threadIdx.x;
+    if ((int64_t)blockIdx.x * 1024 >= n) return;  // uniform per block
+    int32_t *c32 = chunk_box, *c1k = c32 + 6 * (cap / 32 + 1), *c32k = c1k + 6 * (cap / 1024 + 1);
+    int32_t b[6];
+    if (j < n) brick_box(sorted_ids[j], gx, gy, b);
+    else box_empty(b);
+    if (n == 1 && j == 0) write_root(root, -1 - (int32_t)sorted_ids[0], b, B);
 #pragma unroll
-            for (int a = 0; a < 6; ++a) lb[a] = __ldcg(inner_box + 6 * lc + a);
-            lcnt = __ldcg(inner_cnt + lc);
-        }
-        if (rc < 0) {
-            brick_box(__ldg(sorted_ids + (-1 - rc)), gx, gy, rb);
-        } else {
-#pragma unroll
-            for (int a = 0; a < 6; ++a) rb[a] = __ldcg(inner_box + 6 * rc + a);
-            rcnt = __ldcg(inner_cnt + rc);
-        }
-        inner_cnt[p] = lcnt + rcnt;
-        BoxNode nd;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            box[a] = min(lb[a], rb[a]);
-            box[3 + a] = max(lb[3 + a], rb[3 + a]);
-        }
+    for (int a = 0; a < 3; ++a) {
+        b[a] = __reduce_min_sync(0xffffffffu, b[a]);
+        b[3 + a] = __reduce_max_sync(0xffffffffu, b[3 + a]);
+    }
+    __shared__ int32_t wb[32][6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-            inner_box[6 * p + a] = box[a];
-            nd.lbox[a] = (float)(lb[a] * B);
-            nd.rbox[a] = (float)(rb[a] * B);
+            if (j < n) c32[6 * (j >> 5) + a] = b[a];  // chunks that hold a leaf only
+            wb[w][a] = b[a];
         }
-        nd.left = lc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - lc))
-                         : (solid(lcnt, lb) ? solid_ref(lb, gx, gy) : lc);
-        nd.right = rc < 0 ? -1 - (int32_t)__ldg(sorted_ids + (-1 - rc))
-                          : (solid(rcnt, rb) ? solid_ref(rb, gx, gy) : rc);
-        nd.pad0 = nd.pad1 = 0;
-        nodes[p] = nd;
-        if (p == 0) write_root(root, solid(lcnt + rcnt, box) ? solid_ref(box, gx, gy) : 0, box, B);
-        p = __ldcg(parent + p);
     }
+    __syncthreads();
+    if (w == 0) {
+        int32_t t[6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) t[a] = wb[lane][a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t[a] = __reduce_min_sync(0xffffffffu, t[a]);
+            t[3 + a] = __reduce_max_sync(0xffffffffu, t[3 + a]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < 6; ++a) c1k[6 * blockIdx.x + a] = t[a];
+            int32_t *q = c32k + 6 * (blockIdx.x >> 5);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                atomicMax(q + a, LB_BIAS - t[a]);
+                atomicMax(q + 3 + a, t[3 + a]);
+            }
+        }
+    }
+}
+
+// Union of the boxes of sorted leaves [L, R) (L < R) from the chunk tables.
+__device__ __forceinline__ void range_box(int L, int R, const uint32_t *__restrict__ sorted_ids,
+                                          const int32_t *c32, const int32_t *c1k,
+                                          const int32_t *c32k, int gx, int gy, int32_t acc[6])
+{
+    box_empty(acc);
+    int32_t b[6];
+    const int a1 = min((L + 31) & ~31, R), b1 = max(R & ~31, a1);
+    for (int x = L; x < a1; ++x) {
+        brick_box(sorted_ids[x], gx, gy, b);
+        box_add(acc, b);
+    }
+    for (int x = max(b1, a1); x < R; ++x) {
+        brick_box(sorted_ids[x], gx, gy, b);
+        box_add(acc, b);
+    }
+    if (a1 >= b1) return;
+    const int a2 = min((a1 + 1023) & ~1023, b1), b2 = max(b1 & ~1023, a2);
+    for (int x = a1; x < a2; x += 32) box_add(acc, c32 + 6 * (x >> 5));
+    for (int x = b2; x < b1; x += 32) box_add(acc, c32 + 6 * (x >> 5));
+    if (a2 >= b2) return;
+    const int a3 = min((a2 + 32767) & ~32767, b2), b3 = max(b2 & ~32767, a3);
+    for (int x = a2; x < a3; x += 1024) box_add(acc, c1k + 6 * (x >> 10));
+    for (int x = b3; x < b2; x += 1024) box_add(acc, c1k + 6 * (x >> 10));
+    for (int x = a3; x < b3; x += 32768) {
+        const int32_t *q = c32k + 6 * (x >> 15);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            acc[a] = min(acc[a], LB_BIAS - q[a]);
+            acc[3 + a] = max(acc[3 + a], q[3 + a]);
+        }
+    }
+}
+
+// One thread per inner node: its children's boxes from their leaf ranges,
+// then the traversal node (child references, solid subtrees) and the root.
+__global__ void k_lbvh_node_boxes(const uint32_t *__restrict__ sorted_ids,
+                                  const int *__restrict__ count, const int32_t *__restrict__ left,
+                                  const int32_t *__restrict__ right,
+                                  const int32_t *__restrict__ range_end,
+                                  const int32_t *__restrict__ chunk_box, int32_t *inner_box,
+                                  BoxNode *nodes, int32_t *root, int gx, int gy, int B,
+                                  int64_t cap)
+{
+    const int n = *count;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int32_t *c32 = chunk_box, *c1k = c32 + 6 * (cap / 32 + 1),
+                  *c32k = c1k + 6 * (cap / 1024 + 1);
+    const int j = range_end[i], lo = min(i, j), hi = max(i, j);
+    const int lc = left[i], rc = right[i];
+    const int g = lc >= 0 ? lc : -1 - lc;  // left child: leaves [lo, g], right: [g + 1, hi]
+    int32_t lb[6], rb[6], box[6];
+    range_box(lo, g + 1, sorted_ids, c32, c1k, c32k, gx, gy, lb);
+    range_box(g + 1, hi + 1, sorted_ids, c32, c1k, c32k, gx, gy, rb);
+    const int32_t lcnt = g - lo + 1, rcnt = hi - g;
+    BoxNode nd;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        box[a] = min(lb[a], rb[a]);
+        box[3 + a] = max(lb[3 + a], rb[3 + a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        inner_box[6 * i + a] = box[a];
+        nd.lbox[a] = (float)(lb[a] * B);
+        nd.rbox[a] = (float)(rb[a] * B);
+    }
+    nd.left = lc < 0 ? -1 - (int32_t)sorted_ids[-1 - lc]
+                     : (solid(lcnt, lb) ? solid_ref(lb, gx, gy) : lc);
+    nd.right = rc < 0 ? -1 - (int32_t)sorted_ids[-1 - rc]
+                      : (solid(rcnt, rb) ? solid_ref(rb, gx, gy) : rc);
+    nd.pad0 = nd.pad1 = 0;
+    nodes[i] = nd;
+    if (i == 0) write_root(root, solid(lcnt + rcnt, box) ? solid_ref(box, gx, gy) : 0, box, B);
 }
 
 // Height of the tree (levels including root and leaves): each leaf counts its
@@ -431,18 +525,23 @@ void launch_lbvh(Ctx &c, Structure &s)
         std::swap(s.ids_sorted, s.ids_alt);
     }
     unsigned blocks = (unsigned)((cap + 255) / 256);
-    ESS_CUDA(cudaMemsetAsync(s.arrive, 0, sizeof(int) * (size_t)(cap > 1 ? cap - 1 : 1), c.stream));
     {
         Launch L(c, "lbvh_karras");
         k_karras<<<blocks, 256, 0, c.stream>>>(s.keys_sorted, s.count, s.left, s.right, s.parent,
-                                               s.leaf_parent);
+                                               s.leaf_parent, s.range_end);
     }
     {
         Launch L(c, "lbvh_bounds");
-        k_lbvh_bounds<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
-                                                    s.parent, s.leaf_parent, s.arrive,
-                                                    s.inner_box, s.inner_cnt, s.nodes, s.root,
-                                                    s.gx, s.gy, s.p.brick);
+        // the chunk-of-32768 boxes are atomic maxima over zero
+        const size_t c32k = (size_t)cap / 32 + 1 + (size_t)cap / 1024 + 1;
+        ESS_CUDA(cudaMemsetAsync(s.chunk_box + 6 * c32k, 0,
+                                 sizeof(int32_t) * 6 * ((size_t)cap / 32768 + 1), c.stream));
+        k_lbvh_chunks<<<(unsigned)((cap + 1023) / 1024), 1024, 0, c.stream>>>(
+            s.ids_sorted, s.count, s.chunk_box, s.root, s.gx, s.gy, s.p.brick, cap);
+        k_lbvh_node_boxes<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
+                                                        s.range_end, s.chunk_box, s.inner_box,
+                                                        s.nodes, s.root, s.gx, s.gy, s.p.brick,
+                                                        cap);
     }
 }
 
