@@ -174,11 +174,11 @@ __global__ void k_kd_root_init(int32_t *root_box, KdState *st)
     }
 }
 
-__global__ void k_kd_root_reduce(const uint32_t *__restrict__ ids, const int *__restrict__ count,
-                                 int gx, int gy, int32_t *root_box)
+// The tight brick box of bricks i (one per thread, i < n) into root_box by
+// integer min/max atomics, one set per warp.
+__device__ __forceinline__ void kd_root_add(const uint32_t *__restrict__ ids, int n, int i, int gx,
+                                            int gy, int32_t *root_box)
 {
-    int n = *count;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     int v[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
     if (i < n) {
         int c[3];
@@ -199,6 +199,12 @@ __global__ void k_kd_root_reduce(const uint32_t *__restrict__ ids, const int *__
             atomicMax(root_box + 3 + a, v[3 + a]);
         }
     }
+}
+
+__global__ void k_kd_root_reduce(const uint32_t *__restrict__ ids, const int *__restrict__ count,
+                                 int gx, int gy, int32_t *root_box)
+{
+    kd_root_add(ids, *count, blockIdx.x * blockDim.x + threadIdx.x, gx, gy, root_box);
 }
 
 // node 0 record and the slabs of level 0 (no level at all for an empty mask)
@@ -744,6 +750,31 @@ __global__ void __launch_bounds__(256) k_kd_decide_emit4(int32_t *nodes9, int32_
     if (use_handle) cudaGraphSetConditional(handle, next > 0 ? 1u : 0u);
 }
 
+// Traversal layout: one BoxNode per node id (leaf entries unused), children
+// referenced as node ids, leaves as -1 - id; the root record and node count.
+template <bool CG>
+__device__ __forceinline__ void kd_pack_node(const int32_t *nodes9, int i, BoxNode *nodes,
+                                             int32_t *root, int B)
+{
+    const int32_t *rec = nodes9 + 9 * (size_t)i;
+    const int fc = kd_ld<CG>(rec + 8);
+    if (i == 0) {
+        root[0] = fc >= 0 ? 0 : -1;
+        for (int a = 0; a < 6; ++a) root[1 + a] = __float_as_int((float)(kd_ld<CG>(rec + a) * B));
+    }
+    if (fc < 0) return;
+    const int32_t *L = nodes9 + 9 * (size_t)fc, *R = L + 9;
+    BoxNode nd;
+    for (int a = 0; a < 6; ++a) {
+        nd.lbox[a] = (float)(kd_ld<CG>(L + a) * B);
+        nd.rbox[a] = (float)(kd_ld<CG>(R + a) * B);
+    }
+    nd.left = kd_ld<CG>(L + 8) >= 0 ? fc : -1 - fc;
+    nd.right = kd_ld<CG>(R + 8) >= 0 ? fc + 1 : -1 - (fc + 1);
+    nd.pad0 = nd.pad1 = 0;
+    nodes[i] = nd;
+}
+
 // ---------------------------------------------------- persistent 4-bin build
 // The whole level loop of a 4-bin build in one cooperative launch (all blocks
 // resident, one per SM): per level the accumulate step, a grid barrier, the
@@ -786,17 +817,32 @@ __device__ __forceinline__ bool kd_grid_sync(unsigned *bar, unsigned target, uin
 __global__ void __launch_bounds__(KD_PERSIST_THREADS) k_kd_build4(
     const uint32_t *__restrict__ ids, const int *__restrict__ count, int *__restrict__ brick_node,
     int32_t *nodes9, int32_t *slabs0, int32_t *slabs1, unsigned long long *chunk_st, KdState *st,
-    KdParams P, int next_cap, int capacity, int max_levels, uint32_t *status)
+    int32_t *root_box, BoxNode *nodes, int32_t *root, int *m_dev, KdParams P, int next_cap,
+    int capacity, int max_levels, uint32_t *status)
 {
     __shared__ long long s_key[KD_HT_PERSIST];
     __shared__ int s_val[KD_HT_PERSIST][6];
-    int lvl_size = st->lvl_size;  // 1, or 0 for an empty mask (k_kd_init)
-    if (lvl_size <= 0) return;    // uniform
-    const unsigned epoch = st->epoch;
+    const unsigned epoch = st->epoch;  // k_kd_root_init ran before: level state reset
     const int n = *count;
-    int prev_begin = 0, lvl_begin = 0, levels = 0;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
     unsigned target = 0;
-    while (true) {
+    int prev_begin = 0, lvl_begin = 0, levels = 0, lvl_size = n > 0 ? 1 : 0;
+    if (lvl_size > 0) {  // uniform
+        // root: the tight box of all non-empty bricks, node 0 and the level-0 slabs
+        for (int base = 0; base < n; base += gthreads) kd_root_add(ids, n, base + gtid, P.gx, P.gy, root_box);
+        if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
+        if (blockIdx.x == 0) {
+            if (threadIdx.x < 6) nodes9[threadIdx.x] = __ldcg(root_box + threadIdx.x);
+            if (threadIdx.x == 0) {
+                nodes9[6] = -1;
+                nodes9[7] = 0;
+                nodes9[8] = -1;
+            }
+            for (int q = threadIdx.x; q < 3 * 4 * 6; q += blockDim.x) slabs0[q] = 0;
+        }
+        if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
+    }
+    while (lvl_size > 0) {  // uniform
         int32_t *cur = (levels & 1) ? slabs1 : slabs0, *nxt = (levels & 1) ? slabs0 : slabs1;
         kd_accumulate_level<4, true, KD_HT_PERSIST>(ids, n, brick_node, nodes9, cur, prev_begin,
                                                     lvl_begin, lvl_size, P, s_key, s_val);
@@ -816,9 +862,12 @@ __global__ void __launch_bounds__(KD_PERSIST_THREADS) k_kd_build4(
             next = 0;
         }
         lvl_size = next;
-        if (lvl_size == 0) break;  // uniform
     }
+    // traversal layout of the finished tree (every record was written before
+    // the last barrier)
+    for (int i = gtid; i < lvl_begin; i += gthreads) kd_pack_node<true>(nodes9, i, nodes, root, P.B);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *m_dev = lvl_begin;
         st->prev_begin = prev_begin;
         st->lvl_begin = lvl_begin;
         st->lvl_size = 0;
@@ -927,8 +976,7 @@ __global__ void __launch_bounds__(256) k_kd_emit(const KdDecision *__restrict__ 
 }
 
 
-// Traversal layout: one BoxNode per node id (leaf entries unused), children
-// referenced as node ids, leaves as -1 - id; the root record and node count.
+// Traversal layout (kd_pack_node), one thread per node.
 __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const KdState *st, int *m_dev,
                           BoxNode *nodes, int32_t *root, int B)
 {
@@ -936,23 +984,7 @@ __global__ void k_kd_pack(const int32_t *__restrict__ nodes9, const KdState *st,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *m_dev = m;
     if (i >= m) return;
-    const int32_t *rec = nodes9 + 9 * (size_t)i;
-    if (i == 0) {
-        root[0] = rec[8] >= 0 ? 0 : -1;
-        for (int a = 0; a < 6; ++a) root[1 + a] = __float_as_int((float)(rec[a] * B));
-    }
-    int fc = rec[8];
-    if (fc < 0) return;
-    const int32_t *L = nodes9 + 9 * (size_t)fc, *R = L + 9;
-    BoxNode nd;
-    for (int a = 0; a < 6; ++a) {
-        nd.lbox[a] = (float)(L[a] * B);
-        nd.rbox[a] = (float)(R[a] * B);
-    }
-    nd.left = L[8] >= 0 ? fc : -1 - fc;
-    nd.right = R[8] >= 0 ? fc + 1 : -1 - (fc + 1);
-    nd.pad0 = nd.pad1 = 0;
-    nodes[i] = nd;
+    kd_pack_node<false>(nodes9, i, nodes, root, B);
 }
 
 // ------------------------------------------------------------------ host
@@ -1154,7 +1186,7 @@ static void kd_build_persistent(Ctx &c, Structure &s, const KdParams &P, int blo
     kd_full_buffers(c, s, P);
     const size_t cap = (size_t)s.nb;
     KdState *st = (KdState *)s.kd_state;
-    kd_root_launches(c, s, P, (unsigned)((cap + 255) / 256));
+    k_kd_root_init<<<1, 32, 0, c.stream>>>(s.kd_scratch_i32, st);  // resets the barrier counter
     int next_cap = (int)std::min(s.kd_slab_cap[0], s.kd_slab_cap[1]);
     int capacity = s.kd_capacity, max_levels = KD_MAX_LEVELS;
     KdParams Pk = P;
@@ -1164,12 +1196,13 @@ static void kd_build_persistent(Ctx &c, Structure &s, const KdParams &P, int blo
     int32_t *nodes9 = s.kd_nodes, *s0 = s.kd_slabs[0], *s1 = s.kd_slabs[1];
     unsigned long long *chunk = s.kd_chunk;
     uint32_t *status = c.dev_status;
-    void *args[] = {&ids, &count, &brick_node, &nodes9, &s0, &s1, &chunk, &st,
-                    &Pk, &next_cap, &capacity, &max_levels, &status};
+    int32_t *root_box = s.kd_scratch_i32, *root = s.root;
+    BoxNode *nodes = s.nodes;
+    int *m_dev = s.kd_count_dev;
+    void *args[] = {&ids, &count, &brick_node, &nodes9, &s0, &s1, &chunk, &st, &root_box,
+                    &nodes, &root, &m_dev, &Pk, &next_cap, &capacity, &max_levels, &status};
     ESS_CUDA(cudaLaunchCooperativeKernel((const void *)k_kd_build4, dim3((unsigned)blocks),
                                          dim3(KD_PERSIST_THREADS), args, 0, c.stream));
-    k_kd_pack<<<(unsigned)((2 * cap + 255) / 256), 256, 0, c.stream>>>(
-        s.kd_nodes, (const KdState *)s.kd_state, s.kd_count_dev, s.nodes, s.root, P.B);
 }
 
 static void kd_build_graph(Ctx &c, Structure &s, const KdParams &P)
