@@ -45,9 +45,11 @@ struct KdParams {
     int S;        // slab slots per axis
 };
 
-struct KdDecision {
+// A node's decision; in the persistent build also the record through which
+// its bricks move to a child (fc: the first child, -1 for a leaf), 64 bytes.
+struct __align__(16) KdDecision {
     int32_t split;  // 1 if the node splits
-    int32_t axis, plane;
+    int32_t axis, plane, fc;
     int32_t L[6], R[6];
 };
 
@@ -515,7 +517,8 @@ __device__ __forceinline__ void kd_decide_emit4_level(int32_t *nodes9, const int
                                                       const KdParams &P, int next_cap,
                                                       int capacity, uint32_t *status,
                                                       int lvl_begin, int lvl_size,
-                                                      unsigned long long tag)
+                                                      unsigned long long tag,
+                                                      KdDecision *moves = nullptr)
 {
     constexpr int S = 4;
     static_assert(CH <= 32, "one ballot covers a chunk's nodes");
@@ -688,6 +691,7 @@ __device__ __forceinline__ void kd_decide_emit4_level(int32_t *nodes9, const int
             const int fc = lvl_begin + lvl_size + 2 * (s_excl + rank);
             if (fc + 1 >= capacity) {
                 atomicOr(status, DEV_ERR_OVERFLOW);
+                if (moves) moves[ch * CH + threadIdx.x].fc = -1;
             } else {
                 const KdDecision &d = sdec[threadIdx.x];
                 int32_t *rec = nodes9 + 9 * (size_t)(lvl_begin + ch * CH + threadIdx.x);
@@ -703,7 +707,14 @@ __device__ __forceinline__ void kd_decide_emit4_level(int32_t *nodes9, const int
                 cl[6] = cr[6] = -1;
                 cl[7] = cr[7] = 0;
                 cl[8] = cr[8] = -1;
+                if (moves) {
+                    KdDecision m = d;
+                    m.fc = fc;
+                    moves[ch * CH + threadIdx.x] = m;
+                }
             }
+        } else if (moves && threadIdx.x < CH && ch * CH + (int)threadIdx.x < lvl_size) {
+            moves[ch * CH + threadIdx.x].fc = -1;  // a leaf: its bricks stay
         }
         __syncthreads();  // sdec and s_excl are rewritten by the next chunk
     }
@@ -775,6 +786,112 @@ __device__ __forceinline__ void kd_pack_node(const int32_t *nodes9, int i, BoxNo
     nodes[i] = nd;
 }
 
+// The accumulate step of the persistent build: each thread keeps the nodes
+// of its bricks (i = k x threads + its index, k < KMAX) in registers across
+// the levels when the bricks fit (reg), and a brick of a node split on the
+// previous level reads one 64-byte move record (its node's decision, first
+// child and both children's boxes) instead of the node record and then the
+// child's record.  Same slab updates as kd_accumulate_level.
+template <int KMAX>
+__device__ __forceinline__ void kd_accumulate_persist(
+    const uint32_t *__restrict__ ids, int n, int *__restrict__ brick_node, int (&node_r)[KMAX],
+    bool reg, const KdDecision *moves, const int32_t *root_rec, int32_t *slabs, int prev_begin,
+    int lvl_begin, int lvl_size, const KdParams &P, long long *s_key, int (*s_val)[6])
+{
+    constexpr int HT = KD_HT_PERSIST, HB = 10;
+    static_assert(HT == (1 << HB), "hash bits");
+    for (int h = threadIdx.x; h < HT; h += blockDim.x) {
+        s_key[h] = -1;
+        for (int k = 0; k < 6; ++k) s_val[h][k] = 0;
+    }
+    __syncthreads();
+    const int gthreads = gridDim.x * blockDim.x;
+    auto brick = [&](int i, int &node) {
+        bool live = i < n;
+        int c[3] = {0, 0, 0};
+        int32_t box[6];
+        if (live) {
+            brick_coords(ids[i], P.gx, P.gy, c);
+            if (lvl_begin == 0) {
+                node = 0;
+            } else if (node >= prev_begin && node < lvl_begin) {
+                const int4 *mv = reinterpret_cast<const int4 *>(moves + (node - prev_begin));
+                const int4 h = __ldcg(mv);  // split, axis, plane, fc
+                if (h.w >= 0) {
+                    const int side = c[h.y] >= h.z ? 1 : 0;
+                    node = h.w + side;
+                    const int4 q1 = __ldcg(mv + 1), q2 = __ldcg(mv + 2), q3 = __ldcg(mv + 3);
+                    // L = q1.xyzw q2.xy, R = q2.zw q3.xyzw
+                    box[0] = side ? q2.z : q1.x;
+                    box[1] = side ? q2.w : q1.y;
+                    box[2] = side ? q3.x : q1.z;
+                    box[3] = side ? q3.y : q1.w;
+                    box[4] = side ? q3.z : q2.x;
+                    box[5] = side ? q3.w : q2.y;
+                }
+            }
+            if (node < lvl_begin || node >= lvl_begin + lvl_size) live = false;
+        }
+        if (lvl_begin == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) box[k] = root_rec[k];
+        }
+        const int local = node - lvl_begin;
+        const int v[6] = {KD_LO_BIAS - c[0], KD_LO_BIAS - c[1], KD_LO_BIAS - c[2],
+                          c[0] + 1, c[1] + 1, c[2] + 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bool use = live && box[3 + a] - box[a] >= 2;
+            int sl = use ? kd_slab_of(c[a], box[a], box[3 + a], 4) : 0;
+            long long slot_id = use ? ((long long)local * 3 + a) * P.S + sl : -1;
+            long long first = __shfl_sync(0xffffffffu, slot_id, 0);
+            if (__all_sync(0xffffffffu, slot_id == first)) {
+                if (first < 0) continue;
+                int r[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) r[k] = __reduce_max_sync(0xffffffffu, v[k]);
+                if ((threadIdx.x & 31) == 0) slab_atomic(slabs + 6 * first, r);
+            } else if (use) {
+                int h = (int)((unsigned long long)(slot_id * 0x9E3779B97F4A7C15ull) >> (64 - HB));
+                bool done = false;
+                for (int probe = 0; probe < 8 && !done; ++probe, h = (h + 1) & (HT - 1)) {
+                    long long old = atomicCAS((unsigned long long *)&s_key[h], (unsigned long long)-1ll,
+                                              (unsigned long long)slot_id);
+                    if (old == -1 || old == slot_id) {
+                        for (int k = 0; k < 6; ++k) atomicMax(&s_val[h][k], v[k]);
+                        done = true;
+                    }
+                }
+                if (!done) slab_atomic(slabs + 6 * slot_id, v);
+            }
+        }
+    };
+    if (reg) {
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int base = k * gthreads + blockIdx.x * blockDim.x;
+            if (base >= n) break;  // uniform per block
+            brick(base + threadIdx.x, node_r[k]);
+        }
+    } else {
+        for (int base = blockIdx.x * blockDim.x; base < n; base += gthreads) {
+            const int i = base + threadIdx.x;
+            int node = i < n && lvl_begin > 0 ? brick_node[i] : 0;
+            brick(i, node);
+            if (i < n) brick_node[i] = node;
+        }
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < HT; h += blockDim.x) {
+        long long key = s_key[h];
+        if (key >= 0) {
+            int r[6];
+            for (int k = 0; k < 6; ++k) r[k] = s_val[h][k];
+            slab_atomic(slabs + 6 * key, r);
+        }
+    }
+}
+
 // ---------------------------------------------------- persistent 4-bin build
 // The whole level loop of a 4-bin build in one cooperative launch (all blocks
 // resident, one per SM): per level the accumulate step, a grid barrier, the
@@ -817,9 +934,10 @@ __device__ __forceinline__ bool kd_grid_sync(unsigned *bar, unsigned target, uin
 __global__ void __launch_bounds__(KD_PERSIST_THREADS) k_kd_build4(
     const uint32_t *__restrict__ ids, const int *__restrict__ count, int *__restrict__ brick_node,
     int32_t *nodes9, int32_t *slabs0, int32_t *slabs1, unsigned long long *chunk_st, KdState *st,
-    int32_t *root_box, BoxNode *nodes, int32_t *root, int *m_dev, KdParams P, int next_cap,
-    int capacity, int max_levels, uint32_t *status)
+    int32_t *root_box, BoxNode *nodes, int32_t *root, int *m_dev, KdDecision *moves, KdParams P,
+    int next_cap, int capacity, int max_levels, uint32_t *status)
 {
+    constexpr int KMAX = 8;  // bricks per thread whose nodes stay in registers
     __shared__ long long s_key[KD_HT_PERSIST];
     __shared__ int s_val[KD_HT_PERSIST][6];
     const unsigned epoch = st->epoch;  // k_kd_root_init ran before: level state reset
@@ -842,15 +960,23 @@ __global__ void __launch_bounds__(KD_PERSIST_THREADS) k_kd_build4(
         }
         if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
     }
+    int node_r[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) node_r[k] = 0;
+    const bool reg = (long long)n <= (long long)KMAX * gthreads;
+    int32_t root_rec[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) root_rec[k] = lvl_size > 0 ? __ldcg(nodes9 + k) : 0;
     while (lvl_size > 0) {  // uniform
         int32_t *cur = (levels & 1) ? slabs1 : slabs0, *nxt = (levels & 1) ? slabs0 : slabs1;
-        kd_accumulate_level<4, true, KD_HT_PERSIST>(ids, n, brick_node, nodes9, cur, prev_begin,
-                                                    lvl_begin, lvl_size, P, s_key, s_val);
+        kd_accumulate_persist<KMAX>(ids, n, brick_node, node_r, reg, moves, root_rec, cur,
+                                    prev_begin, lvl_begin, lvl_size, P, s_key, s_val);
         if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
         const unsigned long long tag = ((unsigned long long)((epoch << 8) | (unsigned)levels)) << 32;
         kd_decide_emit4_level<true, KD_PERSIST_THREADS / 16>(nodes9, cur, nxt, chunk_st,
                                                              &st->splits, P, next_cap, capacity,
-                                                             status, lvl_begin, lvl_size, tag);
+                                                             status, lvl_begin, lvl_size, tag,
+                                                             moves);
         if (!kd_grid_sync(&st->bar, target += gridDim.x, status)) return;
         // st->splits is rewritten only after the next level's first barrier
         int next = 2 * *(volatile int *)&st->splits;
@@ -1199,8 +1325,10 @@ static void kd_build_persistent(Ctx &c, Structure &s, const KdParams &P, int blo
     int32_t *root_box = s.kd_scratch_i32, *root = s.root;
     BoxNode *nodes = s.nodes;
     int *m_dev = s.kd_count_dev;
+    KdDecision *moves = (KdDecision *)s.kd_dec;  // one per node of a level (kd_full_buffers)
     void *args[] = {&ids, &count, &brick_node, &nodes9, &s0, &s1, &chunk, &st, &root_box,
-                    &nodes, &root, &m_dev, &Pk, &next_cap, &capacity, &max_levels, &status};
+                    &nodes, &root, &m_dev, &moves, &Pk, &next_cap, &capacity, &max_levels,
+                    &status};
     ESS_CUDA(cudaLaunchCooperativeKernel((const void *)k_kd_build4, dim3((unsigned)blocks),
                                          dim3(KD_PERSIST_THREADS), args, 0, c.stream));
 }
