@@ -846,29 +846,31 @@ __device__ __forceinline__ void trace_walk(const RArgs &a, const Ray &r, float t
         const int m = __reduce_min_sync(lanes, alive ? held : 0x7fffffff);
         if (m == 0x7fffffff) break;  // every lane's ray is done
         if (alive) {
-            float kf = (float)k;
-            for (int j = 0; j < m; ++j) {
+            float kf = (float)k, kend = (float)rg.r0.y;
+            int j = 0;
+            for (; j < m; ++j) {
                 const float t = fmaf(kf, a.dt, tn);
                 if (!(t < tf)) {
                     alive = false;
                     break;
                 }
-                ++ns;
                 SampleFetch<T, SAMPLER> f;
                 f.fetch(a, r, t);
                 if (composite<T, SAMPLER, SHADE>(a, r, t, f.value(a), acc)) {
                     alive = false;
+                    ++j;
                     break;
                 }
-                if (k == rg.r0.y) {
+                if (__builtin_expect(kf == kend, 0)) {
                     rg.pop_front();
-                    k = rg.r0.x;  // meaningless once the queue is empty (held is 0 then)
-                    kf = (float)k;
+                    kf = (float)rg.r0.x;  // meaningless once the queue is empty (held is 0 then)
+                    kend = (float)rg.r0.y;
                 } else {
-                    ++k;
                     kf += 1.0f;
                 }
             }
+            k = (int)kf;
+            ns += j;
             held -= m;
         }
     }
