@@ -1254,6 +1254,11 @@ def run_ours(args, rank, local, ws, dist):
                                  cores)
         result["cpu_baseline"] = {"value": rate, "unit": "samples/s", "cores": cores,
                                   "kind": "oracle", "sample": desc}
+        # the same marcher on one core, for the per-core rate
+        rate1, desc1 = oracle_rate(vol_host, vlo, vhi, tfs_np[0], views[0][0], w,
+                                   min(args.ref_budget, 1.5), 1)
+        result["cpu_baseline"]["single_core"] = {"value": rate1, "unit": "samples/s",
+                                                 "sample": desc1}
     with torch.cuda.stream(stream):
         ess.ess_destroy(ctx)
     if rank == 0:
