@@ -1013,7 +1013,8 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
             j.out = it.out;
             j.tile_w = tw;
             const int shaded = render_shaded(it.params) ? 1 : 0;
-            groups[(((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)) * 2 + shaded]
+            groups[((((int)v.dtype * 16 + (int)s.kind) * 2 + (v.use_cells ? 1 : 0)) * 2 + shaded) *
+                       2 + (s.kind == ESS_GRID && grid_dda_inc(j) ? 1 : 0)]
                 .push_back(j);
         }
         for (int i = 0; i < count; ++i) join_build(c, get_st(c, items[i].structure));
@@ -1046,7 +1047,7 @@ ess_status ess_render_batch(ess_ctx *ctx, const ess_render_item *items, int coun
                     if (e1 == cudaSuccess)
                         launch_render_batch(c, jobs[0].st->kind, jobs[0].vol->dtype,
                                             jobs[0].vol->use_cells, render_shaded(jobs[0].rp),
-                                            g.dev);
+                                            (kv.first & 1) != 0, g.dev);
                 } catch (...) {
                     c.stream = saved;
                     cudaGraph_t tmp;

@@ -296,7 +296,10 @@ void launch_render(Ctx &c, const RenderJob &job);
 constexpr int BATCH_MAX = 4096;
 size_t batch_bytes(int n);
 size_t pack_batch(Ctx &c, const RenderJob *jobs, int n, int tw, void *host, size_t cap);
-void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, bool shaded, void *dev);
+// Whether a grid render job may use the walk that advances its crossings.
+bool grid_dda_inc(const RenderJob &j);
+void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, bool shaded, bool dda_inc,
+                         void *dev);
 // Whether the render needs the shaded kernels (shading, or an opacity
 // correction that changes alpha).
 bool render_shaded(const ess_render_params &rp);

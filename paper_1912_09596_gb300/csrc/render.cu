@@ -24,6 +24,26 @@
 
 namespace ess {
 
+// Whether the grid walk may advance its crossings (GridWalkT<true>): the
+// drift after every step it can take stays below a quarter of the sample step.
+// t_max is the largest ray parameter of a sample: the farthest volume corner
+// from the eye plus the image plane's extent (orthographic origins).
+bool grid_dda_inc(const RenderJob &j)
+{
+    double tmax = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        const double cx = (k & 1) ? j.vol->nx : 0, cy = (k & 2) ? j.vol->ny : 0,
+                     cz = (k & 4) ? j.vol->nz : 0;
+        const double dx = cx - j.cam.eye[0], dy = cy - j.cam.eye[1], dz = cz - j.cam.eye[2];
+        tmax = std::max(tmax, std::sqrt(dx * dx + dy * dy + dz * dz));
+    }
+    double ext = 0.0;
+    for (int i = 0; i < 3; ++i) ext += std::fabs(j.cam.u[i]) + std::fabs(j.cam.v[i]);
+    tmax += ext;
+    const double steps = (double)j.st->gx + j.st->gy + j.st->gz + 4.0;
+    return steps * tmax * std::ldexp(1.0, -24) <= 0.25 * j.rp.dt;
+}
+
 static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
 {
     a.vol = j.vol->data;
@@ -58,22 +78,7 @@ static void fill_args(Ctx &c, const RenderJob &j, RArgs &a)
     a.gx = j.st->gx;
     a.gy = j.st->gy;
     a.gz = j.st->gz;
-    {
-        // largest ray parameter of a sample: the farthest volume corner from
-        // the eye, plus the image plane's extent (orthographic origins)
-        double tmax = 0.0;
-        for (int k = 0; k < 8; ++k) {
-            const double cx = (k & 1) ? j.vol->nx : 0, cy = (k & 2) ? j.vol->ny : 0,
-                         cz = (k & 4) ? j.vol->nz : 0;
-            const double dx = cx - j.cam.eye[0], dy = cy - j.cam.eye[1], dz = cz - j.cam.eye[2];
-            tmax = std::max(tmax, std::sqrt(dx * dx + dy * dy + dz * dz));
-        }
-        double ext = 0.0;
-        for (int i = 0; i < 3; ++i) ext += std::fabs(j.cam.u[i]) + std::fabs(j.cam.v[i]);
-        tmax += ext;
-        const double steps = (double)a.gx + a.gy + a.gz + 4.0;
-        a.dda_inc = steps * tmax * std::ldexp(1.0, -24) <= 0.25 * j.rp.dt ? 1 : 0;
-    }
+    a.dda_inc = grid_dda_inc(j) ? 1 : 0;
     a.nodes = j.st->nodes;
     a.root = j.st->root;
     a.count = (j.st->kind == ESS_KD || j.st->kind == ESS_HYBRID) ? j.st->kd_count_dev : j.st->count;
@@ -156,19 +161,20 @@ size_t pack_batch(Ctx &c, const RenderJob *jobs, int n, int tw, void *host, size
 
 // Persistent launch over a packed batch already copied to `dev` (same
 // layout).
-void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, bool shaded, void *dev)
+void launch_render_batch(Ctx &c, int kind, ess_dtype dt, bool cells, bool shaded, bool dda_inc,
+                         void *dev)
 {
     size_t prefix_bytes = batch_prefix_bytes();
     char *p = (char *)dev;
     BatchHeader *h = (BatchHeader *)p;
     const int *prefix = (const int *)(p + sizeof(BatchHeader));
     const RArgs *args = (const RArgs *)(p + sizeof(BatchHeader) + prefix_bytes);
-    if (shaded) launch_batch_kernels<1>(c, kind, dt, cells, args, prefix, h);
-    else launch_batch_kernels<0>(c, kind, dt, cells, args, prefix, h);
+    if (shaded) launch_batch_kernels<1>(c, kind, dt, cells, dda_inc, args, prefix, h);
+    else launch_batch_kernels<0>(c, kind, dt, cells, dda_inc, args, prefix, h);
 }
 
 template void launch_render_kernels<0>(Ctx &, const RArgs &, int, ess_dtype, int);
-template void launch_batch_kernels<0>(Ctx &, int, ess_dtype, bool, const RArgs *, const int *,
+template void launch_batch_kernels<0>(Ctx &, int, ess_dtype, bool, bool, const RArgs *, const int *,
                                       BatchHeader *);
 
 }  // namespace ess

@@ -1046,7 +1046,8 @@ template <int SHADE> void launch_render_kernels(Ctx &c, const RArgs &a, int kind
 
 // Persistent launch over a packed batch: every SM filled to its occupancy.
 template <int SHADE>
-void launch_batch_kernels(Ctx &c, int kind, ess_dtype dt, bool cells, const RArgs *args,
+void launch_batch_kernels(Ctx &c, int kind, ess_dtype dt, bool cells, bool dda_inc,
+                          const RArgs *args,
                           const int *prefix, BatchHeader *h)
 {
     int sms = 0, per_sm = 0;
@@ -1071,7 +1072,17 @@ void launch_batch_kernels(Ctx &c, int kind, ess_dtype dt, bool cells, const RArg
     }
     switch (kind) {
     case ESS_NONE: ESS_BATCH_T(ESS_NONE); break;
-    case ESS_GRID: ESS_BATCH_T(ESS_GRID); break;
+    case ESS_GRID:
+        if (dda_inc && cells) {  // every item of the batch allows advanced crossings
+            switch (dt) {
+            case ESS_U8: ESS_BATCH_S(uint8_t, 1, KIND_GRID_INC); break;
+            case ESS_U16: ESS_BATCH_S(uint16_t, 1, KIND_GRID_INC); break;
+            default: ESS_BATCH_S(float, 1, KIND_GRID_INC); break;
+            }
+        } else {
+            ESS_BATCH_T(ESS_GRID);
+        }
+        break;
     case ESS_LBVH: ESS_BATCH_T(ESS_LBVH); break;
     case ESS_HYBRID: ESS_BATCH_T(ESS_HYBRID); break;
     default: ESS_BATCH_T(ESS_KD); break;
@@ -1083,9 +1094,9 @@ void launch_batch_kernels(Ctx &c, int kind, ess_dtype dt, bool cells, const RArg
 
 extern template void launch_render_kernels<0>(Ctx &, const RArgs &, int, ess_dtype, int);
 extern template void launch_render_kernels<1>(Ctx &, const RArgs &, int, ess_dtype, int);
-extern template void launch_batch_kernels<0>(Ctx &, int, ess_dtype, bool, const RArgs *,
+extern template void launch_batch_kernels<0>(Ctx &, int, ess_dtype, bool, bool, const RArgs *,
                                              const int *, BatchHeader *);
-extern template void launch_batch_kernels<1>(Ctx &, int, ess_dtype, bool, const RArgs *,
+extern template void launch_batch_kernels<1>(Ctx &, int, ess_dtype, bool, bool, const RArgs *,
                                              const int *, BatchHeader *);
 
 }  // namespace ess

@@ -6,7 +6,7 @@
 namespace ess {
 
 template void launch_render_kernels<1>(Ctx &, const RArgs &, int, ess_dtype, int);
-template void launch_batch_kernels<1>(Ctx &, int, ess_dtype, bool, const RArgs *, const int *,
+template void launch_batch_kernels<1>(Ctx &, int, ess_dtype, bool, bool, const RArgs *, const int *,
                                       BatchHeader *);
 
 }  // namespace ess
