@@ -284,8 +284,9 @@ __global__ void k_karras(const uint32_t *__restrict__ k, const int *__restrict__
 // the union of the leaf boxes in that range (the same values a bottom-up
 // union gives).  The leaves are cut into chunks of 32, 1024 and 32768; a
 // first pass stores every chunk's box, and each inner node then unions its
-// two children's ranges from at most 31 leaves, 31 + 31 chunks of 32, 31 +
-// 31 chunks of 1024 and the chunks of 32768 between them.  No step waits for
+// two children's ranges from at most 31 + 31 leaves, 31 + 31 chunks of 32,
+// 31 + 31 chunks of 1024 and the chunks of 32768 between them, one warp per
+// node.  No step waits for
 // another node, unlike a bottom-up pass whose threads climb one level per
 // dependent atomic.
 //
@@ -399,61 +400,68 @@ __global__ void __launch_bounds__(1024) k_lbvh_chunks(const uint32_t *__restrict
     }
 }
 
-// Union of the boxes of sorted leaves [L, R) (L < R) from the chunk tables.
-__device__ __forceinline__ void range_box(int L, int R, const uint32_t *__restrict__ sorted_ids,
-                                          const int32_t *c32, const int32_t *c1k,
-                                          const int32_t *c32k, int gx, int gy, int32_t acc[6])
+// Union of the boxes of sorted leaves [L, R) (L < R) from the chunk tables,
+// taken by a whole warp: [L, R) splits into at most 31 leaves, 31 chunks of 32
+// and 31 chunks of 1024 on each side and the chunks of 32768 between, and
+// lane l takes item l of every part (the chunks of 32768 by a stride of 32),
+// so every load of a node is issued at once.  All lanes receive the box.
+__device__ __forceinline__ void warp_range_box(int L, int R, const uint32_t *__restrict__ sorted_ids,
+                                               const int32_t *c32, const int32_t *c1k,
+                                               const int32_t *c32k, int gx, int gy, int lane,
+                                               int32_t acc[6])
 {
     box_empty(acc);
     int32_t b[6];
     const int a1 = min((L + 31) & ~31, R), b1 = max(R & ~31, a1);
-    for (int x = L; x < a1; ++x) {
-        brick_box(sorted_ids[x], gx, gy, b);
+    if (L + lane < a1) {
+        brick_box(sorted_ids[L + lane], gx, gy, b);
         box_add(acc, b);
     }
-    for (int x = max(b1, a1); x < R; ++x) {
-        brick_box(sorted_ids[x], gx, gy, b);
+    if (b1 + lane < R) {
+        brick_box(sorted_ids[b1 + lane], gx, gy, b);
         box_add(acc, b);
     }
-    if (a1 >= b1) return;
-    const int a2 = min((a1 + 1023) & ~1023, b1), b2 = max(b1 & ~1023, a2);
-    for (int x = a1; x < a2; x += 32) box_add(acc, c32 + 6 * (x >> 5));
-    for (int x = b2; x < b1; x += 32) box_add(acc, c32 + 6 * (x >> 5));
-    if (a2 >= b2) return;
-    const int a3 = min((a2 + 32767) & ~32767, b2), b3 = max(b2 & ~32767, a3);
-    for (int x = a2; x < a3; x += 1024) box_add(acc, c1k + 6 * (x >> 10));
-    for (int x = b3; x < b2; x += 1024) box_add(acc, c1k + 6 * (x >> 10));
-    for (int x = a3; x < b3; x += 32768) {
-        const int32_t *q = c32k + 6 * (x >> 15);
+    if (a1 < b1) {
+        const int a2 = min((a1 + 1023) & ~1023, b1), b2 = max(b1 & ~1023, a2);
+        if (a1 + 32 * lane < a2) box_add(acc, c32 + 6 * ((a1 >> 5) + lane));
+        if (b2 + 32 * lane < b1) box_add(acc, c32 + 6 * ((b2 >> 5) + lane));
+        if (a2 < b2) {
+            const int a3 = min((a2 + 32767) & ~32767, b2), b3 = max(b2 & ~32767, a3);
+            if (a2 + 1024 * lane < a3) box_add(acc, c1k + 6 * ((a2 >> 10) + lane));
+            if (b3 + 1024 * lane < b2) box_add(acc, c1k + 6 * ((b3 >> 10) + lane));
+            for (int x = a3 + 32768 * lane; x < b3; x += 32 * 32768) {
+                const int32_t *q = c32k + 6 * (x >> 15);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            acc[a] = min(acc[a], LB_BIAS - q[a]);
-            acc[3 + a] = max(acc[3 + a], q[3 + a]);
+                for (int a = 0; a < 3; ++a) {
+                    acc[a] = min(acc[a], LB_BIAS - q[a]);
+                    acc[3 + a] = max(acc[3 + a], q[3 + a]);
+                }
+            }
         }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[a] = __reduce_min_sync(0xffffffffu, acc[a]);
+        acc[3 + a] = __reduce_max_sync(0xffffffffu, acc[3 + a]);
     }
 }
 
-// One thread per inner node: its children's boxes from their leaf ranges,
-// then the traversal node (child references, solid subtrees) and the root.
-__global__ void k_lbvh_node_boxes(const uint32_t *__restrict__ sorted_ids,
-                                  const int *__restrict__ count, const int32_t *__restrict__ left,
-                                  const int32_t *__restrict__ right,
-                                  const int32_t *__restrict__ range_end,
-                                  const int32_t *__restrict__ chunk_box, int32_t *inner_box,
-                                  BoxNode *nodes, int32_t *root, int gx, int gy, int B,
-                                  int64_t cap)
+// The boxes and traversal node of inner node i (a whole warp; lane 0 writes).
+__device__ __forceinline__ void lbvh_node_box(int i, int lane, const uint32_t *__restrict__ sorted_ids,
+                                              const int32_t *__restrict__ left,
+                                              const int32_t *__restrict__ right,
+                                              const int32_t *__restrict__ range_end,
+                                              const int32_t *c32, const int32_t *c1k,
+                                              const int32_t *c32k, int32_t *inner_box,
+                                              BoxNode *nodes, int32_t *root, int gx, int gy, int B)
 {
-    const int n = *count;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    const int32_t *c32 = chunk_box, *c1k = c32 + 6 * (cap / 32 + 1),
-                  *c32k = c1k + 6 * (cap / 1024 + 1);
     const int j = range_end[i], lo = min(i, j), hi = max(i, j);
     const int lc = left[i], rc = right[i];
     const int g = lc >= 0 ? lc : -1 - lc;  // left child: leaves [lo, g], right: [g + 1, hi]
     int32_t lb[6], rb[6], box[6];
-    range_box(lo, g + 1, sorted_ids, c32, c1k, c32k, gx, gy, lb);
-    range_box(g + 1, hi + 1, sorted_ids, c32, c1k, c32k, gx, gy, rb);
+    warp_range_box(lo, g + 1, sorted_ids, c32, c1k, c32k, gx, gy, lane, lb);
+    warp_range_box(g + 1, hi + 1, sorted_ids, c32, c1k, c32k, gx, gy, lane, rb);
+    if (lane != 0) return;
     const int32_t lcnt = g - lo + 1, rcnt = hi - g;
     BoxNode nd;
 #pragma unroll
@@ -474,6 +482,26 @@ __global__ void k_lbvh_node_boxes(const uint32_t *__restrict__ sorted_ids,
     nd.pad0 = nd.pad1 = 0;
     nodes[i] = nd;
     if (i == 0) write_root(root, solid(lcnt + rcnt, box) ? solid_ref(box, gx, gy) : 0, box, B);
+}
+
+// One warp per inner node: its children's boxes from their leaf ranges, then
+// the traversal node (child references, solid subtrees) and the root.
+__global__ void k_lbvh_node_boxes(const uint32_t *__restrict__ sorted_ids,
+                                  const int *__restrict__ count, const int32_t *__restrict__ left,
+                                  const int32_t *__restrict__ right,
+                                  const int32_t *__restrict__ range_end,
+                                  const int32_t *__restrict__ chunk_box, int32_t *inner_box,
+                                  BoxNode *nodes, int32_t *root, int gx, int gy, int B,
+                                  int64_t cap)
+{
+    const int n = *count;
+    const int lane = threadIdx.x & 31;
+    const int32_t *c32 = chunk_box, *c1k = c32 + 6 * (cap / 32 + 1),
+                  *c32k = c1k + 6 * (cap / 1024 + 1);
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n - 1; i += warps)
+        lbvh_node_box(i, lane, sorted_ids, left, right, range_end, c32, c1k, c32k, inner_box,
+                      nodes, root, gx, gy, B);
 }
 
 // Height of the tree (levels including root and leaves): each leaf counts its
@@ -538,7 +566,12 @@ void launch_lbvh(Ctx &c, Structure &s)
                                  sizeof(int32_t) * 6 * ((size_t)cap / 32768 + 1), c.stream));
         k_lbvh_chunks<<<(unsigned)((cap + 1023) / 1024), 1024, 0, c.stream>>>(
             s.ids_sorted, s.count, s.chunk_box, s.root, s.gx, s.gy, s.p.brick, cap);
-        k_lbvh_node_boxes<<<blocks, 256, 0, c.stream>>>(s.ids_sorted, s.count, s.left, s.right,
+        int sms = 0;
+        ESS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+        const unsigned nb_warps =
+            (unsigned)std::min<int64_t>((32 * (int64_t)cap + 255) / 256, 16 * (int64_t)sms);
+        k_lbvh_node_boxes<<<nb_warps, 256, 0, c.stream>>>(
+            s.ids_sorted, s.count, s.left, s.right,
                                                         s.range_end, s.chunk_box, s.inner_box,
                                                         s.nodes, s.root, s.gx, s.gy, s.p.brick,
                                                         cap);
