@@ -114,3 +114,27 @@ def test_kd_render_matches_oracle_and_naive(gpu, ctx, ora, ert):
                 assert np.array_equal(bits(got), bits(render(ess, torch, ctx, naive, cam, W, H,
                                                              ert=ert)))
             ess.ess_release(ctx, st)
+
+
+@pytest.mark.parametrize("threshold", [8, 9])
+def test_kd_and_lbvh_over_258k_bricks(gpu, ctx, ora, threshold):
+    """Over 155,648 non-empty bricks (2^3 bricks of a 128^3 volume, nearly all
+    non-empty): the cooperative k-d build keeps its bricks' nodes in a device
+    array instead of registers, and the LBVH's node boxes use chunks of 32768
+    leaves.  Both trees equal the oracle's, and the images the naive march."""
+    from test_gpu_lbvh import check_lbvh
+    ess, torch = gpu
+    v = synth.blobs_u8((128, 128, 128), n_blobs=12, seed=21)
+    tf = synth.tf_ramp(256, threshold)
+    vol, t = upload(ess, torch, ctx, v, 0, 255, tf)
+    ov, ot = ora.OVolume(v, 0, 255), ora.OTF(tf)
+    mask = ora.build_mask(ov, ot, 2)
+    assert int(mask.sum()) > 4 * 152 * 256
+    st, _, _ = check_kd(gpu, ctx, ora, v, 0, 255, tf, 2, 4, 1, 32)
+    lb = ess.ess_build(ctx, vol, t, ess.LBVH, ess.build_params(brick=2))
+    check_lbvh(ess, ctx, lb, ora.lbvh_build(mask, ov.grid(2)))
+    naive = ess.ess_build(ctx, vol, t, ess.NONE)
+    cam = synth.orbit_camera(ov.dims, 48, 40, theta=0.7, phi=0.3)
+    ref = render(ess, torch, ctx, naive, cam, 48, 40)
+    for s in (st, lb):
+        assert np.array_equal(bits(render(ess, torch, ctx, s, cam, 48, 40)), bits(ref))
