@@ -20,7 +20,9 @@
  *  - Output images are caller-owned float32 RGBA buffers, W*H*4 floats, row
  *    major, row 0 at the top.  `out_on_device` says whether `out` is device
  *    memory (written asynchronously on the context stream) or host memory
- *    (the call copies the image back and returns when it is there).
+ *    (the call returns when the image is there: pinned memory that the
+ *    context's device can address is written by the render kernel itself,
+ *    other host memory through a device staging buffer and a copy).
  *  - Device memory that the library allocates belongs to the context and is
  *    returned by ess_release() / ess_destroy().
  *  - Work is issued asynchronously on the context's CUDA stream, in call

@@ -965,10 +965,27 @@ ess_status ess_render(ess_ctx *ctx, ess_handle structure, const ess_camera *came
         j.H = H;
         j.tile_w = params->tile_w;
         size_t bytes = (size_t)W * H * 4 * sizeof(float);
+        // host memory the device can address (pinned: cudaMallocHost or
+        // cudaHostRegister) is written by the render itself over the host
+        // link, with no staging copy; other host memory takes the copy
+        float *host_dev = nullptr;
+        if (!out_on_device) {
+            cudaPointerAttributes pa{};
+            if (cudaPointerGetAttributes(&pa, out) == cudaSuccess) {
+                if (pa.type == cudaMemoryTypeHost && pa.devicePointer)  // for this device
+                    host_dev = (float *)pa.devicePointer;
+            } else {
+                cudaGetLastError();  // not a CUDA pointer: the copy path
+            }
+        }
         if (out_on_device) {
             j.out = out;
             launch_render(c, j);
             mark(c, s.used);
+        } else if (host_dev) {
+            j.out = host_dev;
+            launch_render(c, j);
+            ESS_CUDA(cudaStreamSynchronize(c.stream));
         } else {
             if (c.stage_bytes < bytes) {
                 c.free(c.stage);
