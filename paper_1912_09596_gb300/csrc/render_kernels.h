@@ -429,12 +429,26 @@ __device__ __forceinline__ float correct_alpha(float alpha, float r)
 // then two-sided Blinn-Phong under a headlight (light and eye along -d):
 // c = min(|n . d|, 1), rgb' = rgb (ka + kd c) + ks c^shininess.  A zero
 // gradient leaves the colour.
-template <typename T, int SAMPLER>
+template <typename T, int SAMPLER, bool INSIDE>
 __device__ __forceinline__ float value_at(const RArgs &a, float px, float py, float pz)
 {
     SampleFetch<T, SAMPLER> f;
-    f.at(a, px, py, pz);
+    f.template at<INSIDE>(a, px, py, pz);
     return f.value(a);
+}
+
+// Central differences one voxel apart (R13).  INSIDE: every neighbour lies in
+// the volume box [0, n], so its cell needs no per-axis clamp.
+template <typename T, int SAMPLER, bool INSIDE>
+__device__ __forceinline__ void gradient(const RArgs &a, float px, float py, float pz, float &gx,
+                                         float &gy, float &gz)
+{
+    gx = (value_at<T, SAMPLER, INSIDE>(a, px + 1.0f, py, pz) -
+          value_at<T, SAMPLER, INSIDE>(a, px - 1.0f, py, pz)) * 0.5f;
+    gy = (value_at<T, SAMPLER, INSIDE>(a, px, py + 1.0f, pz) -
+          value_at<T, SAMPLER, INSIDE>(a, px, py - 1.0f, pz)) * 0.5f;
+    gz = (value_at<T, SAMPLER, INSIDE>(a, px, py, pz + 1.0f) -
+          value_at<T, SAMPLER, INSIDE>(a, px, py, pz - 1.0f)) * 0.5f;
 }
 
 template <typename T, int SAMPLER>
@@ -442,12 +456,13 @@ __device__ __forceinline__ void shade(const RArgs &a, const Ray &r, float t, flo
 {
     const float px = fmaf(t, r.d[0], r.o[0]), py = fmaf(t, r.d[1], r.o[1]),
                 pz = fmaf(t, r.d[2], r.o[2]);
-    const float gx = (value_at<T, SAMPLER>(a, px + 1.0f, py, pz) -
-                      value_at<T, SAMPLER>(a, px - 1.0f, py, pz)) * 0.5f;
-    const float gy = (value_at<T, SAMPLER>(a, px, py + 1.0f, pz) -
-                      value_at<T, SAMPLER>(a, px, py - 1.0f, pz)) * 0.5f;
-    const float gz = (value_at<T, SAMPLER>(a, px, py, pz + 1.0f) -
-                      value_at<T, SAMPLER>(a, px, py, pz - 1.0f)) * 0.5f;
+    // a sample at least one voxel inside the box on every axis: p +- 1 stays
+    // in [0, n] (float rounding is monotone), so the fast cell index applies
+    const bool inside = px >= 1.0f && px <= (float)a.nx - 1.0f && py >= 1.0f &&
+                        py <= (float)a.ny - 1.0f && pz >= 1.0f && pz <= (float)a.nz - 1.0f;
+    float gx, gy, gz;
+    if (inside) gradient<T, SAMPLER, true>(a, px, py, pz, gx, gy, gz);
+    else gradient<T, SAMPLER, false>(a, px, py, pz, gx, gy, gz);
     const float len2 = fmaf(gz, gz, fmaf(gy, gy, gx * gx));
     if (!(len2 > 0.0f)) return;
     const float len = sqrtf(len2);
