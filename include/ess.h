@@ -352,7 +352,8 @@ typedef struct {
  * and TF edits of resident volumes).  A worker thread admits queued requests
  * in arrival order into batches while their output memory fits the budget,
  * applies the batch's edits (TF upload + rebuild), renders the batch in one
- * persistent launch and copies each image to its host buffer; up to
+ * persistent launch and copies each image to its host buffer (a pinned
+ * buffer the device can address is written by the render itself); up to
  * max_inflight batches run on the GPU while the next one is admitted.  Each
  * image equals what ess_render gives for the request alone.  While the server
  * runs, the context must not be used directly; destroy the server before the

@@ -44,6 +44,7 @@ struct Req {
     int done = 0;
     ess_status status = ESS_OK;
     float *dev_out = nullptr;
+    bool direct = false;  // dev_out is the device's address of the caller's pinned image
     size_t out_bytes = 0;
 };
 
@@ -166,8 +167,21 @@ void issue(ess_server *s, std::vector<Req *> &batch)
             if (st == ESS_OK) st = ess_rebuild(ctx, q->r.structure);
         }
         if (st == ESS_OK) {
-            if (cudaMallocFromPoolAsync((void **)&q->dev_out, q->out_bytes, s->pool, c.stream) !=
-                cudaSuccess) {
+            // a pinned image the device can address is written by the render
+            // itself; any other image goes through a pool buffer and a copy
+            cudaPointerAttributes pa{};
+            q->direct = false;
+            if (cudaPointerGetAttributes(&pa, q->r.out) == cudaSuccess) {
+                if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+                    q->dev_out = (float *)pa.devicePointer;
+                    q->direct = true;
+                }
+            } else {
+                cudaGetLastError();
+            }
+            if (!q->direct &&
+                cudaMallocFromPoolAsync((void **)&q->dev_out, q->out_bytes, s->pool, c.stream) !=
+                    cudaSuccess) {
                 cudaGetLastError();
                 q->dev_out = nullptr;
                 st = ESS_ERR_OOM;
@@ -193,7 +207,7 @@ void issue(ess_server *s, std::vector<Req *> &batch)
         if (st != ESS_OK) {
             std::lock_guard<std::mutex> lk(s->mtx);
             for (Req *q : ok) {
-                cudaFreeAsync(q->dev_out, c.stream);
+                if (!q->direct) cudaFreeAsync(q->dev_out, c.stream);
                 q->dev_out = nullptr;
                 finish_request(s, q, st);
             }
@@ -216,6 +230,7 @@ void issue(ess_server *s, std::vector<Req *> &batch)
     cudaEventRecord(rendered, c.stream);
     cudaStreamWaitEvent(s->copy_stream, rendered, 0);
     for (Req *q : ok) {
+        if (q->direct) continue;  // already in the caller's image
         cudaMemcpyAsync(q->r.out, q->dev_out, q->out_bytes, cudaMemcpyDeviceToHost,
                         s->copy_stream);
         cudaFreeAsync(q->dev_out, s->copy_stream);
