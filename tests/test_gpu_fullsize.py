@@ -68,6 +68,24 @@ def test_ct512_masks_and_sampled_pixels(gpu, ctx, ora, ct512):
         ess.ess_release(ctx, t)
 
 
+def test_ct512_cell_vote_masks(gpu, ctx, ora, ct512):
+    """The exact per-cell vote over every brick of the 512^3 workload (8^3
+    bricks: the staged vote, each warp over several bricks) equals the
+    oracle's per-cell mask bit for bit."""
+    ess, torch = gpu
+    vol_np, tfs, _ = ct512
+    ov = ora.OVolume(vol_np, 0, 255)
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(vol_np).cuda(), 0, 255)
+    for ti in (0, 7):
+        t = ess.ess_tf_set(ctx, torch.from_numpy(tfs[ti]).cuda())
+        st = ess.ess_build(ctx, vol, t, ess.GRID, ess.build_params(brick=8, empty_test=1))
+        ref = ora.brick_mask_cells(ov, 8, ora.OTF(tfs[ti]))
+        assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_MASK), ref), ti
+        ess.ess_release(ctx, st)
+        ess.ess_release(ctx, t)
+    ess.ess_release(ctx, vol)
+
+
 def _tree_arrays(ess, ctx, st, kind):
     rd = lambda a: ess.ess_structure_read(ctx, st, a)
     if kind == ess.LBVH:

@@ -49,6 +49,51 @@ def test_minmax_mask_ids_bit_exact(gpu, ctx, ora, case, B):
         ess.ess_release(ctx, st)
 
 
+def _vote_volumes():
+    """Rows of whole bricks (nx a multiple of 8) but ragged in y and z, for the
+    staged vote of 4^3 and 8^3 bricks: mostly-zero volumes whose few
+    non-zero voxels decide the bricks, so a brick's first visible cell row
+    can come in any of its rounds; the 96^3 case has more bricks than the
+    kernel has warps, so that each warp takes several."""
+    rng = np.random.default_rng(31)
+
+    def sparse(shape, vals):
+        return np.where(rng.random(shape) < 0.97, 0, vals(shape))
+
+    yield "u8_40", sparse((19, 21, 40), lambda sh: rng.integers(1, 256, sh)).astype(np.uint8), \
+        (0, 255), 256
+    yield "u16_24", sparse((13, 30, 24), lambda sh: rng.integers(1, 65536, sh)).astype(np.uint16), \
+        (0, 65535), 700
+    yield "f32_16", sparse((22, 11, 16), lambda sh: rng.uniform(0, 1, sh)).astype(np.float32), \
+        (0.0, 1.0), 1024
+    yield "u8_96", synth.blobs_u8((96, 96, 96), n_blobs=12, seed=7), (0, 255), 256
+
+
+@pytest.mark.parametrize("case", list(_vote_volumes()), ids=lambda c: c[0])
+@pytest.mark.parametrize("B", [4, 8])
+def test_vote_staged_bit_exact(gpu, ctx, ora, case, B):
+    """The staged per-cell vote (rows of whole bricks) equals the oracle's per-cell
+    mask bit for bit, under TFs whose first entries are transparent (cells of
+    zeros are invisible) and under a TF that leaves them opaque."""
+    ess, torch = gpu
+    name, v, (lo, hi), nt = case
+    ov = ora.OVolume(v, lo, hi)
+    vol = ess.ess_volume_upload(ctx, torch.from_numpy(v).cuda(), lo, hi)
+    for seed, clear_low in ((1, True), (2, True), (3, False)):
+        tf = synth.tf_random_sparse(nt, seed=seed, p_zero=0.8)
+        if clear_low:
+            tf[:2, 3] = 0.0
+        t = ess.ess_tf_set(ctx, torch.from_numpy(tf).cuda())
+        ref = ora.brick_mask_cells(ov, B, ora.OTF(tf))
+        st = ess.ess_build(ctx, vol, t, ess.GRID, ess.build_params(brick=B, empty_test=1))
+        mask = ess.ess_structure_read(ctx, st, ess.ARR_MASK)
+        assert np.array_equal(mask, ref), (name, B, seed)
+        assert np.array_equal(ess.ess_structure_read(ctx, st, ess.ARR_IDS), ora.compact(ref))
+        ess.ess_release(ctx, st)
+        ess.ess_release(ctx, t)
+    ess.ess_release(ctx, vol)
+
+
 def _row_volumes():
     """Rows of whole 16-byte vectors, more than 32 vectors per row (two warps
     share a brick row) and, for the wide bricks, a ragged last brick in x."""
