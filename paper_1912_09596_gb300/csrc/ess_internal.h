@@ -135,8 +135,10 @@ struct Structure {
     int *kd_count_dev = nullptr;     // device: k-d node count
     int *brick_node = nullptr;       // per non-empty brick: its node on the current level
     int32_t *kd_scratch_i32 = nullptr;  // root box reduction
-    int32_t *kd_slabs[2] = {nullptr, nullptr};  // per-level slab boxes (ping-pong)
-    size_t kd_slab_cap[2] = {0, 0};             // in nodes
+    // per-level slab boxes: ping-pong, and a third buffer for the persistent
+    // build (which zeroes the buffer of level l + 1 during level l)
+    int32_t *kd_slabs[3] = {nullptr, nullptr, nullptr};
+    size_t kd_slab_cap[3] = {0, 0, 0};          // in nodes
     unsigned long long *kd_vr = nullptr;        // suffix volumes
     size_t kd_vr_cap = 0;
     void *kd_dec = nullptr;                     // per-node decisions
