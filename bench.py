@@ -77,6 +77,8 @@ PROFILE_COMMANDS = {
                          "--no-minmax --no-structures --no-shaded --no-cell-vote --no-fractal",
     "step_ct512_vote_batch": "--steps 1 --warmup 1 --no-cpu-baseline --no-serve --no-minmax "
                              "--no-hybrid --no-structures --no-shaded --no-fractal",
+    "step_ct512_vote": "--steps 1 --warmup 1 --no-cpu-baseline --no-batched --no-serve "
+                       "--no-minmax --no-hybrid --no-structures --no-shaded --no-fractal",
     "step_ct512_hybrid_only": "--steps 1 --warmup 1 --no-cpu-baseline --no-batched --no-serve "
                               "--no-minmax --no-structures --no-shaded --no-cell-vote --no-fractal",
     "step_fractal1024": "--workload fractal1024 --steps 1 --warmup 1 --no-cpu-baseline "
