@@ -75,6 +75,23 @@ def test_cell_mask_within_minmax_mask(ora, case):
         assert np.all(cm <= mm)
 
 
+@pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
+def test_cell_mask_equals_minmax_mask(ora, case):
+    """...and in fact equal to it: the cells touching a brick cover its apron
+    voxels, neighbouring cells share corner voxels, and the TF index interval
+    of a range is monotone in its ends, so the cells' intervals overlap in a
+    chain whose union is the brick's own interval; a non-zero entry of that
+    interval lies in some cell's.  A cell range that starts one cell late
+    (no cell c = bB - 1) makes the masks differ on most of these volumes and
+    brick sizes."""
+    name, v, (lo, hi), tf = case
+    vol, otf = ora.OVolume(v, lo, hi), ora.OTF(tf)
+    for B in (2, 3, 4, 5, 8):
+        mm = ora.build_mask(vol, otf, B)
+        cm = ora.brick_mask_cells(vol, B, otf)
+        assert np.array_equal(cm, mm), (name, B)
+
+
 @pytest.mark.parametrize("dtype", ["u8", "f32"])
 @pytest.mark.parametrize("B", [3, 4, 8])
 def test_minmax_matches_numpy(ora, dtype, B):
