@@ -62,6 +62,9 @@ def _vote_volumes():
 
     yield "u8_40", sparse((19, 21, 40), lambda sh: rng.integers(1, 256, sh)).astype(np.uint8), \
         (0, 255), 256
+    # rows of whole 16-byte blocks: the two-block row loads of 8-bit voxels
+    yield "u8_48", sparse((19, 21, 48), lambda sh: rng.integers(1, 256, sh)).astype(np.uint8), \
+        (0, 255), 256
     yield "u16_24", sparse((13, 30, 24), lambda sh: rng.integers(1, 65536, sh)).astype(np.uint16), \
         (0, 65535), 700
     yield "f32_16", sparse((22, 11, 16), lambda sh: rng.uniform(0, 1, sh)).astype(np.float32), \
